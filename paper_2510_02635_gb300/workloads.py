@@ -1,0 +1,96 @@
+"""Named workloads and their seeded synthetic inputs.
+
+This module holds no arithmetic of the method.  It only names the problem
+parameters of each workload and draws the query points x0 (and the terminal
+coefficients theta) from numpy's seeded generator, so that the CUDA path, the
+CPU oracle, the tests and the benchmark all see identical inputs.  The Brownian
+increments of the method itself are not drawn here: both implementations
+regenerate them from the counter-based Philox4x32-10 stream.
+
+The paper has no dataset: all its experiments are manufactured closed-form
+problems (Sec. 4), and these workloads are of the same kind.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: str            # problem kind (see the C-ABI header for the formulas)
+    d: int
+    sigma: float
+    T: float
+    N: int
+    M: int
+    Q: int               # number of independent query points (solves)
+    seed: int            # Philox seed of the Brownian increments and of the inputs
+    x0_law: str          # "zero", "normal_1/d" (N(0, I/d)), "uniform_pm1" (U[-1,1]^d)
+    precision: str = "fp32"   # "fp32": FP32 streams + FP64 solve/Newton; "fp64": FP64 throughout
+    h: float = 2.0
+    ridge_rel: float = 1e-3
+    cg_tol: float = 1e-6
+    cg_max_iter: int = 0  # 0: library default
+    newton_tol: float = 1e-13
+    newton_max_iter: int = 50
+    A: float = 0.0
+    c0: float = 0.0
+    c1: float = 0.0
+    theta_law: str | None = None   # "uniform_0.5_1.5" for the log-quadratic terminal
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def particle_dim_updates(self) -> int:
+        """Q * M * d * N: particle-dimension updates of one whole solve."""
+        return self.Q * self.M * self.d * self.N
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def inputs(w: Workload) -> dict:
+    """Seeded query points x0 [Q, d] (float64) and, if the terminal needs them,
+    coefficients theta [d]."""
+    rng = np.random.default_rng(w.seed)
+    theta = None
+    if w.theta_law == "uniform_0.5_1.5":
+        theta = rng.uniform(0.5, 1.5, size=w.d)
+    if w.x0_law == "zero":
+        x0 = np.zeros((w.Q, w.d))
+    elif w.x0_law == "normal_1/d":
+        x0 = rng.standard_normal((w.Q, w.d)) / math.sqrt(w.d)
+    elif w.x0_law == "uniform_pm1":
+        x0 = rng.uniform(-1.0, 1.0, size=(w.Q, w.d))
+    else:
+        raise ValueError(f"unknown x0 law {w.x0_law!r}")
+    if w.extra.get("theta_affine"):
+        theta = rng.uniform(-1.0, 1.0, size=w.d)
+    return {"x0": np.ascontiguousarray(x0), "theta": theta}
+
+
+# Plain scheme at d = 100, FP64 throughout (Allen-Cahn with manufactured source).
+C0_AC_D100 = Workload("ac_manufactured_d100_M2048_N10_Q1_fp64", "ac_manufactured", d=100,
+                      sigma=1.0, T=0.5, N=10, M=2048, Q=1, seed=0, x0_law="zero",
+                      precision="fp64", cg_tol=1e-12)
+# Gradient-dependent driver at d = 1000; sigma = d makes the logistic closed form exact.
+C1_LOGISTIC_D1000 = Workload("logistic_grad_d1000_M4096_N20_Q64", "logistic_grad", d=1000,
+                             sigma=1000.0, T=1.0, N=20, M=4096, Q=64, seed=1,
+                             x0_law="normal_1/d")
+# Very high dimension: the Allen-Cahn problem of C0 at d = 10^4.
+C2_AC_D10000 = Workload("ac_manufactured_d10000_M16384_N50_Q16", "ac_manufactured", d=10000,
+                        sigma=1.0, T=1.0, N=50, M=16384, Q=16, seed=2, x0_law="uniform_pm1")
+# Log-quadratic terminal with the quadratic-gradient driver (Cole-Hopf solvable).
+C4_HJB_D1000 = Workload("hjb_logquad_d1000_M4096_N20_Q1", "hjb_logquad", d=1000,
+                        sigma=math.sqrt(2.0), T=1.0, N=20, M=4096, Q=1, seed=4,
+                        x0_law="normal_1/d", theta_law="uniform_0.5_1.5")
+# Sec. 4.1, case 1 of the paper: double-well Allen-Cahn, d = 100, T = 0.3, x0 = 0,
+# generator Lap u (sigma = sqrt 2); printed reference u(0,0) ~ 0.0528.
+AC_CASE1_D100 = Workload("ac_doublewell_d100_T0.3", "ac_doublewell", d=100,
+                         sigma=math.sqrt(2.0), T=0.3, N=10, M=2048, Q=1, seed=5, x0_law="zero")
+
+ALL = {w.name: w for w in (C0_AC_D100, C1_LOGISTIC_D1000, C2_AC_D10000, C4_HJB_D1000,
+                           AC_CASE1_D100)}
