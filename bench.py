@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput of the localized FBSDE hot path on GB300 (one JSON line on stdout).
+
+A step is one whole solve (Algorithm 1: forward sweep + all N backward levels) of
+the d = 10^4 Allen-Cahn workload: Q = 16 query points, M = 16384 particles each,
+N = 50 steps, FP32 particle stream with FP64 regression solve and Newton.
+Metric: particle-dim updates per second = Q M d N / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU (torchrun, one rank per GPU): the query points shard across ranks with no
+collective on the data path (weak scaling: every rank solves its own 16 queries);
+the step time is the maximum over ranks.  The reference arm (--impl reference) times
+the FP64 CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2510_02635_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = W.C2_AC_D10000
+METRIC = "particle-dim updates/sec (K*M*d per step)"
+UNIT = "particle-dim updates/s"
+
+
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_uuid(torch) -> str | None:
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(w: W.Workload, levels: int = 2) -> dict:
+    """The FP64 oracle on one query of the workload: the full forward sweep and `levels`
+    backward levels, timed per phase; the whole-solve time is extrapolated as
+    t_forward + N t_level, so value = M d N / that time."""
+    import oracle
+    inp = W.inputs(w)
+    p = oracle.Problem(w.kind, w.d, w.sigma, w.T, w.N, w.M, theta=inp["theta"], h=w.h,
+                       ridge_rel=w.ridge_rel, cg_tol=1e-12)
+    t0 = time.perf_counter()
+    r = oracle.solve(p, inp["x0"][0], w.seed, 0, max_levels=levels)
+    wall = time.perf_counter() - t0
+    t_level = r["backward_s"] / levels
+    t_full = r["forward_s"] + w.N * t_level
+    return {"value": w.M * w.d * w.N / t_full, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle", "wall_s": wall, "forward_s": r["forward_s"],
+            "level_s": t_level,
+            "sample": (f"1 of {w.Q} queries (d={w.d}, M={w.M}), full forward sweep of "
+                       f"N={w.N} steps + {levels} backward levels in FP64, whole-solve time "
+                       f"extrapolated as t_fwd + N*t_level")}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    w = WORKLOAD
+    for _ in range(args.warmup):
+        oracle_sample(w, levels=1)
+    vals, wall = [], 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(w, levels=1)
+        vals.append(s["value"])
+        wall += s["wall_s"]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "d": w.d, "M": w.M, "N": w.N,
+                                            "Q": 1, "sample": s["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                             "sample": s["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank: int, world: int) -> None:
+    import numpy as np
+    import torch
+
+    from paper_2510_02635_gb300 import build as gbuild
+    from paper_2510_02635_gb300 import fbsde
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if not os.path.exists(fbsde.LIB_PATH):
+        gbuild.build()
+    fbsde.load_library()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = WORKLOAD
+    inp = W.inputs(w)
+    x0 = torch.tensor(inp["x0"], device="cuda")
+    solver = fbsde.Solver(w.kind, w.d, w.N, w.M, w.sigma, w.T, Q=w.Q, precision=w.precision,
+                          theta=inp["theta"], h=w.h, ridge_rel=w.ridge_rel, cg_tol=w.cg_tol,
+                          cg_max_iter=w.cg_max_iter)
+    sidx = rank * w.Q  # each rank owns its own query points / Philox streams
+    stream = torch.cuda.current_stream()
+
+    def step():
+        out = torch.empty(w.Q, dtype=torch.float64, device="cuda")
+        grad = torch.empty(w.Q, w.d, dtype=torch.float64, device="cuda")
+        fbsde.check(fbsde.fbsde_solve(solver.problem, w.Q, x0, w.seed, sidx, out, grad,
+                                      solver.workspace), "fbsde_solve")
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K whole solves, device time by CUDA events on the stream
+    fbsde.fbsde_profile_start(1 << 20)
+    with ClockSampler(_gpu_uuid(torch)) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            u = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    prof = fbsde.fbsde_profile_stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = w.particle_dim_updates * world
+    value = units / (ms * 1e-3)
+
+    # ---- per-level CG iterations of the same solve (deterministic): algorithmic bytes
+    tr = solver.solve(x0, seed=w.seed, solve_index0=sidx, trace=True)
+    cg_iters = tr["cg_iters"].cpu().numpy()
+    status = tr["status"]
+    # matrix-free products per step: one per CG iteration plus the warm-start product
+    # of every level below the top one
+    products = int(cg_iters.sum()) + w.Q * (w.N - 1)
+    mv = prof["matvec"]
+    mv_ms_step = mv["total_ms"] / args.steps
+    bytes_per_product = 4.0 * w.M * w.d   # one FP32 read of the particle cloud
+    achieved = bytes_per_product * products / (mv_ms_step * 1e-3) / 1e9
+    peaks = _peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    launches = sum(v["launches"] for v in prof.values())
+
+    # ---- end to end: the host-buffer entry point (copies inside the timed region)
+    ps = fbsde.make_problem(w.kind, w.d, w.N, w.M, w.sigma, w.T, w.precision,
+                            h=w.h, ridge_rel=w.ridge_rel, cg_tol=w.cg_tol,
+                            cg_max_iter=w.cg_max_iter)
+    need = fbsde.fbsde_workspace_bytes(ps, w.Q) + fbsde.fbsde_host_staging_bytes(ps, w.Q)
+    del solver
+    torch.cuda.empty_cache()
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    x0_h = torch.tensor(inp["x0"]).pin_memory().numpy()
+    u_h = torch.zeros(w.Q, dtype=torch.float64).pin_memory().numpy()
+    g_h = torch.zeros(w.Q, w.d, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st = fbsde.fbsde_solve_host(ps, w.Q, x0_h, w.seed, sidx, u_h, g_h, ws)
+        if st not in (0,):
+            raise RuntimeError(f"fbsde_solve_host: {fbsde.fbsde_status_string(st)}")
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, levels=2)
+        cpu.pop("wall_s")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "d": w.d, "M": w.M, "N": w.N,
+                       "Q_per_gpu": w.Q, "precision": "fp32 stream, fp64 solve/Newton",
+                       "cg_tol": w.cg_tol, "l2": "inputs larger than L2 (10.5 GB state)",
+                       "u0_per_query_ms": ms / w.Q},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(x0_h.nbytes),
+                    "d2h_bytes_per_step": int(u_h.nbytes + g_h.nbytes),
+                    "ms_per_step": 1e3 * e2e_s},
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps,
+            "roofline": {"kernel": "matvec", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_product": bytes_per_product,
+                         "products_per_step": products,
+                         "kernel_ms_per_step": mv_ms_step},
+            "kernels_ms_per_step": {k: v["total_ms"] / args.steps for k, v in prof.items()},
+            "cg_iters_mean": float(cg_iters.mean()), "cg_iters_max": int(cg_iters.max()),
+            "device_status": status,
+            "u0_sample": float(u[0]),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * fbsde.h -- C ABI of the GB300 (sm_103a) library for the localized stochastic
+ * FBSDE scheme of Fang, Sheng, Su and Zhou, "A derivative-free localized
+ * stochastic method for very high dimensional semilinear parabolic PDEs"
+ * (arXiv 2510.02635).
+ *
+ * The library evaluates u(0, x0) and grad u(0, x0) for semilinear parabolic PDEs
+ *     d_t u + 1/2 sigma^2 Lap u + f(t, x, u, sigma^T grad u) = 0,  u(T, .) = g      (Eq. 2.1)
+ * with zero drift and a constant scalar diffusion sigma, by the particle scheme of
+ * Algorithm 1: an Euler-Maruyama cloud of M particles per query point (Eq. 2.7), a
+ * kernel-weighted local linear regression per backward level (Eqs. 2.10-2.15 with the
+ * ridge of Remark 2.2 and the Gaussian kernel of Remark 2.3) solved matrix-free on
+ * its Schur complement (Lemma 3.7, Eqs. 3.19-3.20), Z = sigma^T alpha_x, and a scalar
+ * Newton iteration per particle (Eqs. 2.16-2.17).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  "device" pointers are CUDA global-memory addresses of the
+ *    current device; "host" pointers are ordinary host memory.  The caller owns
+ *    every buffer, including the workspace; the library allocates no device memory.
+ *  - Work is enqueued on the given stream (NULL = the legacy default stream) and
+ *    returns before it completes.  Argument errors are returned synchronously and
+ *    nothing is enqueued.  Errors found on the device (Newton or CG exhaustion,
+ *    non-finite values) are recorded in the workspace and read by
+ *    fbsde_diagnostics() after the stream has been synchronised.
+ *  - No C++ exception crosses this boundary.
+ *  - Deterministic: identical inputs, seed and workspace size give bit-identical
+ *    results (every reduction has a fixed order; no floating-point atomics).
+ *  - One workspace must not be used by two calls that may overlap in time.
+ */
+#ifndef FBSDE_H
+#define FBSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FBSDE_API __attribute__((visibility("default")))
+#else
+#define FBSDE_API
+#endif
+
+typedef struct CUstream_st *fbsde_stream_t; /* the same handle as cudaStream_t */
+
+#define FBSDE_ABI_VERSION 1
+#define FBSDE_MAX_D 16384 /* largest dimension d accepted */
+
+typedef enum {
+    FBSDE_OK = 0,
+    FBSDE_ERR_ARG = 1,        /* invalid argument (synchronous; nothing enqueued)      */
+    FBSDE_ERR_WORKSPACE = 2,  /* workspace missing, misaligned or too small           */
+    FBSDE_ERR_CUDA = 3,       /* a CUDA call failed (launch or copy)                   */
+    FBSDE_ERR_NEWTON = 4,     /* a particle's Newton iteration hit newton_max_iter     */
+    FBSDE_ERR_CG = 5,         /* a level's CG solve hit cg_max_iter before cg_tol      */
+    FBSDE_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up                    */
+    FBSDE_ERR_NONFINITE = 7   /* u(0,x0) or grad u(0,x0) is not finite                 */
+} fbsde_status;
+
+/* Problem kinds: terminal condition g and driver f(t, x, y, z) of (2.1). */
+typedef enum {
+    /* f = y - y^3 + q(t,x), q = u*^3 - (2 - sigma^2/2) u*, g = (1/d) sum cos x_i;
+       exact solution u*(t,x) = e^{t-T} (1/d) sum_i cos x_i (Allen-Cahn with a
+       manufactured source, the form of Eq. 4.1). */
+    FBSDE_AC_MANUFACTURED = 0,
+    /* f = (y - (2+d)/(2d)) sum_i z_i, g = 1/(1 + exp(-(T + sum_i x_i/d)));
+       exact solution logistic(t + sum_i x_i/d) when sigma = d. */
+    FBSDE_LOGISTIC_GRAD = 1,
+    /* f = -|z|^2/2, g = log((1 + sum_i theta_i x_i^2)/2); with sigma = sqrt 2,
+       exp(-u) solves the heat equation (Cole-Hopf). */
+    FBSDE_HJB_LOGQUAD = 2,
+    /* f = c0 + c1 y + c2 sum_i z_i + c3 t, g = A + sum_i theta_i x_i (exactly solvable). */
+    FBSDE_AFFINE_TEST = 3,
+    /* f = y - y^3, g = A (reduces to a scalar backward implicit Euler recursion). */
+    FBSDE_CUBIC_TEST = 4,
+    /* f = y - y^3, g = 1/(2 + 0.4 |x|^2): Sec. 4.1, case 1 (use sigma = sqrt 2). */
+    FBSDE_AC_DOUBLEWELL = 5,
+    /* f = c0 + c1 y, g = (1/d) sum_i cos x_i. */
+    FBSDE_COS_LINEAR_TEST = 6
+} fbsde_kind;
+
+typedef enum {
+    FBSDE_FP32 = 0, /* particle state, increments and moment sums in FP32; regression
+                       combination, CG vectors and Newton in FP64                    */
+    FBSDE_FP64 = 1  /* FP64 throughout                                               */
+} fbsde_precision;
+
+typedef struct {
+    int32_t kind;            /* fbsde_kind                                             */
+    int32_t d;               /* dimension, 1 <= d <= FBSDE_MAX_D                       */
+    int32_t N;               /* number of time steps, dt = T/N, N >= 1                 */
+    int32_t precision;       /* fbsde_precision                                        */
+    int64_t M;               /* particles per query point, M >= 2                      */
+    double sigma;            /* scalar diffusion coefficient, > 0                      */
+    double T;                /* terminal time, > 0                                     */
+    const double *theta;     /* device, d coefficients for HJB_LOGQUAD and AFFINE_TEST;
+                                NULL for the other kinds                               */
+    double A, c0, c1, c2, c3;/* parameters of the test kinds (ignored otherwise)       */
+    double h;                /* kernel bandwidth: eps_k^2 = h^2 sigma^2 d t_{k+1};
+                                h <= 0 or h = inf gives uniform weights                */
+    double ridge_rel;        /* ridge lambda = ridge_rel * tr(Gamma_c) / d, >= 0       */
+    double cg_tol;           /* CG stops when ||r|| <= cg_tol ||rhs||, > 0             */
+    int32_t cg_max_iter;     /* CG iterations per level; 0 selects 200                 */
+    int32_t newton_max_iter; /* Newton iterations per particle; 0 selects 50           */
+    double newton_tol;       /* Newton stops when |dY| <= newton_tol max(1,|Y|); 0 selects 1e-13 */
+} fbsde_problem;
+
+/* Optional per-level outputs of a solve (all device pointers, each may be NULL).
+   Level k (0 <= k < N) is the regression of Y_{k+1} on X_{k+1} - x0 at time t_k. */
+typedef struct {
+    double *alpha;          /* [Q][N]    intercept alpha of level k                      */
+    double *alpha_x;        /* [Q][N][d] slope alpha_x (the grad u estimate) of level k  */
+    int32_t *cg_iters;      /* [Q][N]    CG iterations used at level k                   */
+    int32_t *newton_iters;  /* [Q][N]    most Newton iterations of any particle, level k */
+    double *x_N;            /* [Q][M][d] X_N^j - x0 after the forward sweep              */
+    double *y_N;            /* [Q][M]    Y_N^j = g(X_N^j)                                */
+} fbsde_trace;
+
+typedef struct {
+    int32_t status;         /* first fbsde_status met by any solve (FBSDE_OK if none)    */
+    int32_t solves_cg_exhausted;
+    int32_t max_newton_iters;
+    int32_t reserved;
+} fbsde_diag;
+
+/* Bytes of device workspace that fbsde_solve needs for Q query points of problem P.
+   Returns 0 when the arguments are invalid. */
+FBSDE_API size_t fbsde_workspace_bytes(const fbsde_problem *P, int32_t Q);
+
+/*
+ * Algorithm 1 for Q query points at once (independent solves, one particle cloud
+ * each).  Query q uses the Philox stream of solve index solve_index0 + q.
+ *   x0        device [Q][d]  query points
+ *   seed      Philox4x32-10 key of the Brownian increments
+ *   u0        device [Q]     output u(0, x0_q)
+ *   grad_u0   device [Q][d]  output grad u(0, x0_q) (alpha_x of level 0), or NULL
+ *   trace     optional per-level outputs, or NULL
+ *   workspace device, >= fbsde_workspace_bytes(P, Q) bytes, 256-byte aligned
+ * Returns FBSDE_OK when the work was enqueued.
+ */
+FBSDE_API int fbsde_solve(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                uint32_t solve_index0, double *u0, double *grad_u0, const fbsde_trace *trace,
+                void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
+/*
+ * The same solve with the query points and results in HOST memory: copies x0 to
+ * the device, solves, copies u0 and grad_u0 back and synchronises the stream.
+ * theta (if the kind needs it) is read from P->theta as a HOST pointer here.
+ * grad_u0 may be NULL.  Returns the solve's device status as well (blocking call).
+ */
+FBSDE_API int fbsde_solve_host(const fbsde_problem *P, int32_t Q, const double *x0_host, uint64_t seed,
+                     uint32_t solve_index0, double *u0_host, double *grad_u0_host,
+                     void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
+/* Extra workspace bytes fbsde_solve_host needs on top of fbsde_workspace_bytes. */
+FBSDE_API size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q);
+
+/* Synchronises the stream and reads the device-side status of the last solve that
+   used this workspace. */
+FBSDE_API int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *workspace,
+                      fbsde_diag *out, fbsde_stream_t stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on n counters: ctr device [n][4],
+   key device [2], out device [n][4].  Used to test the generator bit for bit. */
+FBSDE_API int fbsde_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                        fbsde_stream_t stream);
+
+/* The standard normals xi_{s,k,j,i} behind the increments Delta W_k^j = sqrt(dt) xi
+   of Eq. (2.7), exactly as the solver draws them: particles j0..j0+nj-1 of level k
+   of solve s, dimensions 0..d-1.  out: device [nj][d] of float (FBSDE_FP32) or
+   double (FBSDE_FP64). */
+FBSDE_API int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int32_t nj, int32_t d,
+                  int32_t precision, void *out, fbsde_stream_t stream);
+
+/* Kernel families of the solve, for the profiler below. */
+typedef enum {
+    FBSDE_K_SETUP = 0,      /* per-query set-up                                          */
+    FBSDE_K_FORWARD = 1,    /* forward sweep (2.7) + terminal + first moments            */
+    FBSDE_K_UPDATE = 2,     /* level update: reverse step, prediction, Newton, moments   */
+    FBSDE_K_MATVEC = 3,     /* matrix-free product of the regression (Sec. 2.4, Steps 1-2)*/
+    FBSDE_K_MOMENTS = 4,    /* per-query reduction of the moments                        */
+    FBSDE_K_CG_START = 5,   /* warm-start residual                                       */
+    FBSDE_K_CG_STEP = 6,    /* per-query CG vector update                                */
+    FBSDE_K_CG_POST = 7,    /* intercept, Z, outputs                                     */
+    FBSDE_K_TRACE = 8,      /* trace copies                                              */
+    FBSDE_NUM_KERNELS = 9
+} fbsde_kernel_family;
+
+typedef struct {
+    int64_t launches;  /* kernel launches of this family since fbsde_profile_start    */
+    int64_t timed;     /* launches bracketed by CUDA events                           */
+    double total_ms;   /* summed event time of the timed launches                     */
+} fbsde_kernel_stats;
+
+/* Process-wide launch profiler (off by default; not for concurrent solves from several
+   host threads).  After fbsde_profile_start(n), every launch is counted and the first
+   n launches are bracketed by CUDA events recorded on the launching stream.
+   fbsde_profile_stop() waits for the recorded events, fills out[FBSDE_NUM_KERNELS]
+   and switches the profiler off. */
+FBSDE_API int fbsde_profile_start(int32_t max_timed_launches);
+FBSDE_API int fbsde_profile_stop(fbsde_kernel_stats *out);
+FBSDE_API const char *fbsde_kernel_name(int family);
+
+FBSDE_API const char *fbsde_status_string(int status);
+FBSDE_API int fbsde_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBSDE_H */

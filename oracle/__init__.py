@@ -96,7 +96,8 @@ def _load():
                                     C.c_double, C.c_double, C.c_int32, _dp, _dp, _dp, _ip]
             lib.orc_llr.restype = C.c_int
             lib.orc_solve.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32,
-                                      C.c_int32, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp]
+                                      C.c_int32, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp,
+                                      _dp]
             lib.orc_solve.restype = C.c_int
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = C.c_int
@@ -237,11 +238,14 @@ def solve(prob: Problem, x0, seed: int, solve_index: int = 0, max_levels: int | 
     xN = np.zeros((M, d)) if keep_forward else None
     yN = np.zeros(M) if keep_forward else None
     y_lv = np.full((N + 1, M), np.nan) if keep_levels_y else None
+    phase = np.zeros(2)
     ps = prob.c_struct()
     st = _load().orc_solve(C.byref(ps), _ptr(x0), int(seed), int(solve_index), L,
                            C.byref(u0), _ptr(grad), _ptr(a_lv), _ptr(ax_lv),
-                           _ptr(cg_lv, _ip), _ptr(nt_lv, _ip), _ptr(xN), _ptr(yN), _ptr(y_lv))
-    out = {"u0": float(u0.value), "grad": grad, "status": int(st)}
+                           _ptr(cg_lv, _ip), _ptr(nt_lv, _ip), _ptr(xN), _ptr(yN), _ptr(y_lv),
+                           _ptr(phase))
+    out = {"u0": float(u0.value), "grad": grad, "status": int(st),
+           "forward_s": float(phase[0]), "backward_s": float(phase[1]), "levels": L}
     if trace:
         out.update(alpha=a_lv, alpha_x=ax_lv, cg_iters=cg_lv, newton_iters=nt_lv)
     if keep_forward:

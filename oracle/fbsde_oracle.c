@@ -52,10 +52,12 @@
  * Box-Muller transform (Box and Muller, 1958) turns word pairs (0,1) and (2,3) into
  * the normals of dimensions 4q..4q+3.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -425,13 +427,14 @@ int orc_llr(int32_t d, int64_t M, const double *D, const double *Y, double rho_r
  *   newton_lv[N]       most Newton iterations any particle needed at level k
  *   xN[M*d], yN[M]     X_N^j and Y_N^j = g(X_N^j) after the forward sweep
  *   y_lv[(N+1)*M]      Y_k^j for every level reached (row k)
+ *   phase_s[2]         wall seconds of the forward sweep and of the backward levels run
  * Returns ORC_OK or the first error met (NEWTON, CG, NONFINITE); on NEWTON/CG the
  * sweep still runs to the end with the last iterates.
  */
 int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t solve_index,
               int32_t max_levels, double *u0, double *grad_u0, double *alpha_lv,
               double *alphax_lv, int32_t *cg_iters_lv, int32_t *newton_lv, double *xN,
-              double *yN, double *y_lv)
+              double *yN, double *y_lv, double *phase_s)
 {
     const int d = P->d, N = P->N;
     const int64_t M = P->M;
@@ -460,6 +463,8 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
         return ORC_ERR_NOMEM;
     }
     int status = ORC_OK;
+    struct timespec tw0, tw1, tw2;
+    clock_gettime(CLOCK_MONOTONIC, &tw0);
 
     /* forward sweep (2.7): X_0 = x0, X_{k+1} = X_k + sigma sqrt(dt) xi_k */
 #pragma omp parallel
@@ -483,6 +488,7 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
     if (xN) memcpy(xN, X, sizeof(double) * Md);
     if (yN) memcpy(yN, Y, sizeof(double) * M);
     if (y_lv) memcpy(y_lv + (size_t)N * M, Y, sizeof(double) * M);
+    clock_gettime(CLOCK_MONOTONIC, &tw1);
 
     for (int k = N - 1; k >= N - max_levels; --k) {
         const double t_k = k * dt, t_k1 = (k + 1) * dt;
@@ -541,6 +547,11 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
         if (y_lv) memcpy(y_lv + (size_t)k * M, Y, sizeof(double) * M);
     }
 
+    clock_gettime(CLOCK_MONOTONIC, &tw2);
+    if (phase_s) {
+        phase_s[0] = (tw1.tv_sec - tw0.tv_sec) + 1e-9 * (tw1.tv_nsec - tw0.tv_nsec);
+        phase_s[1] = (tw2.tv_sec - tw1.tv_sec) + 1e-9 * (tw2.tv_nsec - tw1.tv_nsec);
+    }
     if (max_levels == N && status != ORC_ERR_NOMEM && status != ORC_ERR_ARG) {
         double s = 0.0;
         for (int64_t j = 0; j < M; ++j) s += Y[j];

@@ -1,0 +1,432 @@
+// fbsde_api.cu -- the C ABI declared in include/fbsde.h: argument checks, workspace
+// layout and the launch sequence of Algorithm 1.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fbsde_kernels.cuh"
+
+namespace fbsde {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Team geometry: a row of nch 16-byte chunks is covered by tw warps holding vpt
+// chunks per thread; narrow rows use one warp per row and 8 rows per CTA.
+bool choose_team(int nch, int &tw, int &vpt, int &teams)
+{
+    constexpr int vmax = 8;
+    if (nch <= 32 * vmax) {
+        tw = 1;
+        vpt = 1;
+        while (32 * vpt < nch) vpt *= 2;
+    } else {
+        vpt = vmax;
+        tw = (nch + 32 * vmax - 1) / (32 * vmax);
+    }
+    if (32 * tw > 512) return false;
+    teams = std::max(1, 256 / (32 * tw));
+    return true;
+}
+
+// check_theta: also require the device theta pointer of the kinds that read it.
+int check_problem(const fbsde_problem *P, int32_t Q, bool check_theta)
+{
+    if (!P || Q < 1 || Q > 65535) return FBSDE_ERR_ARG;
+    if (P->kind < FBSDE_AC_MANUFACTURED || P->kind > FBSDE_COS_LINEAR_TEST) return FBSDE_ERR_ARG;
+    if (P->precision != FBSDE_FP32 && P->precision != FBSDE_FP64) return FBSDE_ERR_ARG;
+    if (P->d < 1 || P->d > FBSDE_MAX_D) return FBSDE_ERR_ARG;
+    if (P->N < 1 || P->M < 2 || P->M > (int64_t)1 << 31) return FBSDE_ERR_ARG;
+    if (!(P->sigma > 0.0) || !std::isfinite(P->sigma)) return FBSDE_ERR_ARG;
+    if (!(P->T > 0.0) || !std::isfinite(P->T)) return FBSDE_ERR_ARG;
+    if (!(P->ridge_rel >= 0.0) || !std::isfinite(P->ridge_rel)) return FBSDE_ERR_ARG;
+    if (!(P->cg_tol > 0.0) || P->cg_max_iter < 0 || P->newton_max_iter < 0) return FBSDE_ERR_ARG;
+    if (!(P->newton_tol >= 0.0)) return FBSDE_ERR_ARG;
+    if (check_theta && (P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) &&
+        !P->theta)
+        return FBSDE_ERR_ARG;
+    return FBSDE_OK;
+}
+
+// Workspace layout; independent of every pointer in P.
+int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
+{
+    const int st = check_problem(P, Q, false);
+    if (st != FBSDE_OK) return st;
+    L = Layout{};
+    L.Q = Q;
+    L.d = P->d;
+    L.N = P->N;
+    L.M = P->M;
+    L.precision = P->precision;
+    L.ld = (P->d + 3) / 4 * 4;
+    L.real_sz = P->precision == FBSDE_FP32 ? sizeof(float) : sizeof(double);
+    const int nch = (int)(L.ld * L.real_sz / 16);
+    if (!choose_team(nch, L.team_warps, L.vpt, L.teams)) return FBSDE_ERR_ARG;
+    L.threads = L.teams * 32 * L.team_warps;
+    const long long gmax = std::max<long long>(1, P->M / kMinRowsPerCta);
+    L.G = (int)std::min<long long>(gmax, std::max(1, (kTargetCtas + Q - 1) / Q));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    const size_t Qs = (size_t)Q, Ms = (size_t)P->M, lds = (size_t)L.ld;
+    L.off_delta = take(Qs * Ms * lds * L.real_sz);
+    L.off_Y = take(Qs * Ms * sizeof(double));
+    L.off_w = take(Qs * Ms * L.real_sz);
+    L.off_part = take(Qs * L.G * kPartVecs * lds * L.real_sz);
+    L.off_spart = take(Qs * L.G * kPartScal * sizeof(double));
+    L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
+    L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
+    L.off_state = take(Qs * sizeof(SolveState));
+    L.total = off;
+    return FBSDE_OK;
+}
+
+Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t seed,
+                   uint32_t solve0, double *u0, double *grad, const fbsde_trace *tr)
+{
+    Params p{};
+    p.kind = P->kind;
+    p.d = P->d;
+    p.ld = L.ld;
+    p.N = P->N;
+    p.G = L.G;
+    p.team_warps = L.team_warps;
+    p.M = P->M;
+    p.sigma = P->sigma;
+    p.T = P->T;
+    p.dt = P->T / P->N;
+    p.sdt = P->sigma * std::sqrt(p.dt);
+    p.A = P->A;
+    p.c0 = P->c0;
+    p.c1 = P->c1;
+    p.c2 = P->c2;
+    p.c3 = P->c3;
+    p.uniform = !(P->h > 0.0) || std::isinf(P->h);
+    p.h2 = p.uniform ? 1.0 : P->h * P->h;
+    p.ridge_rel = P->ridge_rel;
+    p.cg_tol2 = P->cg_tol * P->cg_tol;
+    p.cg_max_iter = P->cg_max_iter > 0 ? P->cg_max_iter : 200;
+    p.newton_max_iter = P->newton_max_iter > 0 ? P->newton_max_iter : 50;
+    p.newton_tol = P->newton_tol > 0.0 ? P->newton_tol : 1e-13;
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.solve0 = solve0;
+    char *base = static_cast<char *>(ws);
+    p.delta = base + L.off_delta;
+    p.Y = reinterpret_cast<double *>(base + L.off_Y);
+    p.w = base + L.off_w;
+    p.part = base + L.off_part;
+    p.spart = reinterpret_cast<double *>(base + L.off_spart);
+    p.vec64 = reinterpret_cast<double *>(base + L.off_vec64);
+    p.vecR = base + L.off_vecR;
+    p.st = reinterpret_cast<SolveState *>(base + L.off_state);
+    p.u0 = u0;
+    p.grad = grad;
+    if (tr) {
+        p.tr_alpha = tr->alpha;
+        p.tr_alpha_x = tr->alpha_x;
+        p.tr_cg = tr->cg_iters;
+        p.tr_newton = tr->newton_iters;
+        p.tr_x_N = tr->x_N;
+        p.tr_y_N = tr->y_N;
+    }
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// Launch profiler: counts launches per kernel family and brackets the first `cap`
+// launches with CUDA events on the launching stream.
+// ---------------------------------------------------------------------------
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    int cap = 0, used = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> fam;
+    int64_t launches[FBSDE_NUM_KERNELS] = {};
+};
+Profiler g_prof;
+
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t s;
+    ProfScope(int family, cudaStream_t st) : s(st)
+    {
+        if (!g_prof.on) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        g_prof.launches[family] += 1;
+        if (g_prof.used < g_prof.cap) {
+            slot = g_prof.used++;
+            g_prof.fam[slot] = family;
+            cudaEventRecord(g_prof.ev[2 * slot], s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (slot >= 0) cudaEventRecord(g_prof.ev[2 * slot + 1], s);
+    }
+};
+
+// Algorithm 1: forward sweep, then the backward levels k = N-1..0, each a regression
+// (moments, warm-started CG on the Schur complement) followed by the particle update.
+template <typename Real>
+cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta, cudaStream_t s)
+{
+    using LR = Launch<Real>;
+    cudaError_t e;
+#define FBSDE_TRY(fam, call)                                                                 \
+    do {                                                                                     \
+        ProfScope ps_(fam, s);                                                               \
+        if ((e = (call)) != cudaSuccess) return e;                                           \
+    } while (0)
+    FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, L.Q, s));
+    FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
+    if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
+    for (int k = p.N - 1; k >= 0; --k) {
+        p.level = k;
+        p.newton_level = (k == p.N - 1) ? -1 : k + 1;
+        p.has_r = (k < p.N - 1) ? 1 : 0;  // warm start from alpha_x of level k+1
+        FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments_finalize(p, L, s));
+        if (p.has_r) {
+            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+            FBSDE_TRY(FBSDE_K_CG_START, LR::cg_start(p, L, s));
+        }
+        for (int it = 0; it < p.cg_max_iter; ++it) {
+            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_finalize(p, L, s));
+        }
+        FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
+        if (k >= 1) FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
+    }
+#undef FBSDE_TRY
+    return cudaSuccess;
+}
+
+int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double *theta,
+               uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
+               const fbsde_trace *trace, void *workspace, size_t workspace_bytes,
+               cudaStream_t stream)
+{
+    Layout L;
+    int st = check_problem(P, Q, false);
+    if (st != FBSDE_OK) return st;
+    if ((P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) && !theta)
+        return FBSDE_ERR_ARG;
+    st = make_layout(P, Q, L);
+    if (st != FBSDE_OK) return st;
+    if (!x0 || !u0) return FBSDE_ERR_ARG;
+    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+        return FBSDE_ERR_WORKSPACE;
+    const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, trace);
+    const cudaError_t e = P->precision == FBSDE_FP32 ? run<float>(p, L, x0, theta, stream)
+                                                     : run<double>(p, L, x0, theta, stream);
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
+__global__ void k_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+        const uint4 o = dev::philox4x32_10(c, key[0], key[1]);
+        out[4 * i] = o.x;
+        out[4 * i + 1] = o.y;
+        out[4 * i + 2] = o.z;
+        out[4 * i + 3] = o.w;
+    }
+}
+
+}  // namespace
+}  // namespace fbsde
+
+using namespace fbsde;
+
+extern "C" {
+
+size_t fbsde_workspace_bytes(const fbsde_problem *P, int32_t Q)
+{
+    Layout L;
+    return make_layout(P, Q, L) == FBSDE_OK ? L.total : 0;
+}
+
+int fbsde_solve(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                uint32_t solve_index0, double *u0, double *grad_u0, const fbsde_trace *trace,
+                void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
+{
+    return solve_impl(P, Q, x0, P ? P->theta : nullptr, seed, solve_index0, u0, grad_u0, trace,
+                      workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q)
+{
+    if (check_problem(P, Q, false) != FBSDE_OK) return 0;
+    const size_t Qs = (size_t)Q, ds = (size_t)P->d;
+    return align_up(Qs * ds * 8, kAlign) * 2 + align_up(Qs * 8, kAlign) + align_up(ds * 8, kAlign);
+}
+
+int fbsde_solve_host(const fbsde_problem *P, int32_t Q, const double *x0_host, uint64_t seed,
+                     uint32_t solve_index0, double *u0_host, double *grad_u0_host,
+                     void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
+{
+    if (!P || !x0_host || !u0_host) return FBSDE_ERR_ARG;
+    const bool needs_theta = P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST;
+    fbsde_problem Pd = *P;
+    Layout L;
+    int st = make_layout(&Pd, Q, L);
+    if (st != FBSDE_OK) return st;
+    const size_t Qs = (size_t)Q, ds = (size_t)P->d;
+    const size_t need = L.total + fbsde_host_staging_bytes(&Pd, Q);
+    if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+        return FBSDE_ERR_WORKSPACE;
+    if (needs_theta && !P->theta) return FBSDE_ERR_ARG;
+    char *stage = static_cast<char *>(workspace) + L.total;
+    double *x0_d = reinterpret_cast<double *>(stage);
+    double *grad_d = reinterpret_cast<double *>(stage + align_up(Qs * ds * 8, kAlign));
+    double *u0_d = reinterpret_cast<double *>(stage + 2 * align_up(Qs * ds * 8, kAlign));
+    double *th_d = reinterpret_cast<double *>(stage + 2 * align_up(Qs * ds * 8, kAlign) +
+                                              align_up(Qs * 8, kAlign));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(x0_d, x0_host, Qs * ds * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    if (needs_theta &&
+        cudaMemcpyAsync(th_d, P->theta, ds * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    Pd.theta = needs_theta ? th_d : nullptr;
+    st = solve_impl(&Pd, Q, x0_d, Pd.theta, seed, solve_index0, u0_d,
+                    grad_u0_host ? grad_d : nullptr, nullptr, workspace, L.total, s);
+    if (st != FBSDE_OK) return st;
+    if (cudaMemcpyAsync(u0_host, u0_d, Qs * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    if (grad_u0_host &&
+        cudaMemcpyAsync(grad_u0_host, grad_d, Qs * ds * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    fbsde_diag dg;
+    st = fbsde_diagnostics(&Pd, Q, workspace, &dg, stream);
+    return st != FBSDE_OK ? st : dg.status;
+}
+
+int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *workspace, fbsde_diag *out,
+                      fbsde_stream_t stream)
+{
+    if (!out) return FBSDE_ERR_ARG;
+    Layout L;
+    const int st = make_layout(P, Q, L);
+    if (st != FBSDE_OK) return st;
+    if (!workspace) return FBSDE_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FBSDE_ERR_CUDA;
+    SolveState *h = new (std::nothrow) SolveState[Q];
+    if (!h) return FBSDE_ERR_ARG;
+    const cudaError_t e = cudaMemcpy(h, static_cast<const char *>(workspace) + L.off_state,
+                                     sizeof(SolveState) * Q, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] h;
+        return FBSDE_ERR_CUDA;
+    }
+    fbsde_diag d{};
+    for (int q = 0; q < Q; ++q) {
+        if (d.status == FBSDE_OK && h[q].status != 0) d.status = h[q].status;
+        d.solves_cg_exhausted += h[q].cg_exhausted ? 1 : 0;
+        d.max_newton_iters = std::max(d.max_newton_iters, h[q].newton_max_all);
+    }
+    delete[] h;
+    *out = d;
+    return FBSDE_OK;
+}
+
+int fbsde_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                        fbsde_stream_t stream)
+{
+    if (!ctr || !key || !out || n < 0) return FBSDE_ERR_ARG;
+    if (n == 0) return FBSDE_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_philox<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(ctr, key, out, n);
+    return cudaGetLastError() == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
+int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int32_t nj, int32_t d,
+                  int32_t precision, void *out, fbsde_stream_t stream)
+{
+    if (!out || nj < 0 || d < 1) return FBSDE_ERR_ARG;
+    if (nj == 0) return FBSDE_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (precision == FBSDE_FP32) e = Launch<float>::normals(seed, s, k, j0, nj, d, out, st);
+    else if (precision == FBSDE_FP64) e = Launch<double>::normals(seed, s, k, j0, nj, d, out, st);
+    else return FBSDE_ERR_ARG;
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
+int fbsde_profile_start(int32_t max_timed_launches)
+{
+    if (max_timed_launches < 0 || max_timed_launches > (1 << 22)) return FBSDE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (cudaEvent_t e : g_prof.ev) cudaEventDestroy(e);
+    g_prof.ev.assign(2 * (size_t)max_timed_launches, nullptr);
+    g_prof.fam.assign((size_t)max_timed_launches, 0);
+    for (auto &e : g_prof.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return FBSDE_ERR_CUDA;
+    g_prof.cap = max_timed_launches;
+    g_prof.used = 0;
+    std::fill(g_prof.launches, g_prof.launches + FBSDE_NUM_KERNELS, 0);
+    g_prof.on = true;
+    return FBSDE_OK;
+}
+
+int fbsde_profile_stop(fbsde_kernel_stats *out)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = false;
+    int st = FBSDE_OK;
+    fbsde_kernel_stats acc[FBSDE_NUM_KERNELS] = {};
+    for (int f = 0; f < FBSDE_NUM_KERNELS; ++f) acc[f].launches = g_prof.launches[f];
+    for (int i = 0; i < g_prof.used; ++i) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(g_prof.ev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) != cudaSuccess) {
+            st = FBSDE_ERR_CUDA;
+            continue;
+        }
+        acc[g_prof.fam[i]].timed += 1;
+        acc[g_prof.fam[i]].total_ms += ms;
+    }
+    for (cudaEvent_t e : g_prof.ev) cudaEventDestroy(e);
+    g_prof.ev.clear();
+    g_prof.fam.clear();
+    g_prof.cap = g_prof.used = 0;
+    if (out) std::memcpy(out, acc, sizeof(acc));
+    return st;
+}
+
+const char *fbsde_kernel_name(int family)
+{
+    static const char *names[FBSDE_NUM_KERNELS] = {"setup",      "forward",  "update",
+                                                   "matvec",     "moments",  "cg_start",
+                                                   "cg_step",    "cg_post",  "trace"};
+    return (family >= 0 && family < FBSDE_NUM_KERNELS) ? names[family] : "unknown";
+}
+
+const char *fbsde_status_string(int status)
+{
+    switch (status) {
+    case FBSDE_OK: return "ok";
+    case FBSDE_ERR_ARG: return "invalid argument";
+    case FBSDE_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case FBSDE_ERR_CUDA: return "CUDA error";
+    case FBSDE_ERR_NEWTON: return "Newton iteration did not converge";
+    case FBSDE_ERR_CG: return "CG did not reach its tolerance";
+    case FBSDE_ERR_TIMEOUT: return "device wait timed out";
+    case FBSDE_ERR_NONFINITE: return "non-finite result";
+    }
+    return "unknown status";
+}
+
+int fbsde_abi_version(void) { return FBSDE_ABI_VERSION; }
+
+}  // extern "C"

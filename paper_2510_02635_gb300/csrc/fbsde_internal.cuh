@@ -1,0 +1,87 @@
+// fbsde_internal.cuh -- shared declarations of the CUDA implementation (not part of the ABI).
+//
+// Data layout in HBM (one workspace, caller-allocated, 256-byte aligned sections):
+//   delta  [Q][M][ld]   Real   particle displacement X_k^j - x0 of the current level
+//   Y      [Q][M]       double Y_k^j of the current level
+//   w      [Q][M]       Real   unnormalised kernel weight of particle j for the next regression
+//   part   [Q][G][3][ld] Real  per-CTA partial d-vectors (moments S, B, R or the CG product)
+//   spart  [Q][G][4]    double per-CTA partial scalars (sum w, sum w (Y - yref), sum w rho)
+//   vec64  [Q][7][ld]   double x (= alpha_x), r, p, S, tA, tB, x0
+//   vecR   [Q][3][ld]   Real   p, x, x0 rounded to the stream precision; then theta [ld]
+//   state  [Q]          SolveState
+// ld = d rounded up to a multiple of 4 (16-byte rows for float and 32-byte rows for
+// double); the padding of every row and vector is kept at zero.
+#pragma once
+#include <cstddef>
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fbsde.h"
+
+namespace fbsde {
+
+constexpr int kPartVecs = 3;
+constexpr int kPartScal = 4;
+constexpr int kVec64 = 7;
+constexpr int kVecR = 3;
+constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
+constexpr int kTargetCtas = 608;   // 4 x 152 SMs: CTAs of one streaming pass over all solves
+constexpr int kMinRowsPerCta = 8;
+
+struct SolveState {
+    double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
+    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all;
+};
+
+struct Layout {
+    int Q, d, ld, N, G, precision, team_warps, vpt, teams, threads;
+    int64_t M;
+    size_t real_sz;
+    size_t off_delta, off_Y, off_w, off_part, off_spart, off_vec64, off_vecR, off_state;
+    size_t total;
+};
+
+// Everything a kernel needs, passed by value.
+struct Params {
+    // problem
+    int kind, d, ld, N, G, team_warps, level, uniform, cg_max_iter, newton_max_iter, has_r,
+        newton_level;
+    long long M;
+    double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
+    uint32_t key0, key1, solve0;
+    // workspace
+    void *delta;
+    double *Y;
+    void *w;
+    void *part;
+    double *spart;
+    double *vec64;
+    void *vecR;
+    SolveState *st;
+    // outputs
+    double *u0, *grad;
+    double *tr_alpha, *tr_alpha_x, *tr_x_N, *tr_y_N;
+    int32_t *tr_cg, *tr_newton;
+};
+
+// Host-side launchers, one set per stream precision (defined in fbsde_kernels.cu).
+template <typename Real> struct Launch {
+    static cudaError_t setup(const Params &p, const double *x0, const double *theta, int Q,
+                             cudaStream_t s);
+    static cudaError_t forward(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t update(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t moments_finalize(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t cg_start(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t cg_finalize(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
+                               void *out, cudaStream_t st);
+};
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                          cudaStream_t s);
+
+}  // namespace fbsde

@@ -1,0 +1,984 @@
+// fbsde_kernels.cuh -- CUDA kernels of the localized FBSDE scheme, templated on the
+// precision Real of the particle stream (float or double).  Included once per
+// precision by fbsde_kernels_f32.cu / fbsde_kernels_f64.cu.
+//
+// Work decomposition of the streaming kernels (forward sweep, per-level update and
+// the matrix-free product of the CG solve): grid (G, Q) with CTA (g, s) owning the
+// particle rows [M g / G, M (g+1) / G) of solve s.  A CTA holds one or more "teams"
+// of warps; a team owns one particle row at a time, each thread holding VPT 16-byte
+// chunks of it in registers (chunk c = lane_in_team + team_threads * v).  Per-row
+// sums (dot products, norms, the terminal/driver features) are reduced with a warp
+// butterfly plus, for multi-warp teams, one named barrier.  Each team accumulates its
+// d-vectors in registers; the CTA writes their sum as one partial that the
+// one-CTA-per-solve kernels reduce in a fixed order in FP64.
+#pragma once
+#include <math.h>
+
+#include "fbsde_internal.cuh"
+
+namespace fbsde {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// products whose halves are xored with the other two words and the round key; the
+// key advances by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// 32-bit word -> ((x >> 9) + 1/2) 2^-23 in (0,1), exact in binary32.
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return (__uint2float_rn(x >> 9) + 0.5f) * 0x1p-23f;
+}
+__device__ __forceinline__ double u01d(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * 0x1p-23;
+}
+
+// Box-Muller (1958): (a, b) -> sqrt(-2 ln u_a) (cos, sin)(2 pi u_b).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float r = sqrtf(-2.0f * logf(u01f(a)));
+    float sn, cs;
+    sincospif(2.0f * u01f(b), &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &z0, double &z1)
+{
+    const double r = sqrt(-2.0 * log(u01d(a)));
+    double sn, cs;
+    sincospi(2.0 * u01d(b), &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+// 16 bytes of a particle row: 4 floats or 2 doubles.
+template <typename Real> struct alignas(16) Chunk {
+    static constexpr int E = 16 / sizeof(Real);
+    Real v[E];
+};
+
+template <typename Real> __device__ __forceinline__ Chunk<Real> ld_chunk(const Real *p)
+{
+    Chunk<Real> c;
+    *reinterpret_cast<int4 *>(c.v) = *reinterpret_cast<const int4 *>(p);
+    return c;
+}
+template <typename Real> __device__ __forceinline__ Chunk<Real> ldg_chunk(const Real *p)
+{
+    Chunk<Real> c;
+    *reinterpret_cast<int4 *>(c.v) = __ldg(reinterpret_cast<const int4 *>(p));
+    return c;
+}
+template <typename Real> __device__ __forceinline__ void st_chunk(Real *p, const Chunk<Real> &c)
+{
+    *reinterpret_cast<int4 *>(p) = *reinterpret_cast<const int4 *>(c.v);
+}
+template <typename Real> __device__ __forceinline__ void zero(Chunk<Real> &c)
+{
+#pragma unroll
+    for (int e = 0; e < Chunk<Real>::E; ++e) c.v[e] = Real(0);
+}
+
+// Normals xi_{s,k,j,i} for the elements i of chunk c (counter (i/4, j, k, s)); the
+// elements at i >= d are zero.
+__device__ __forceinline__ Chunk<float> normal_chunk(Chunk<float> *, int c, uint32_t j, uint32_t k,
+                                                     uint32_t s, uint32_t k0, uint32_t k1, int d)
+{
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)c, j, k, s), k0, k1);
+    Chunk<float> z;
+    box_muller(w.x, w.y, z.v[0], z.v[1]);
+    box_muller(w.z, w.w, z.v[2], z.v[3]);
+    const int i0 = 4 * c;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (i0 + e >= d) z.v[e] = 0.0f;
+    return z;
+}
+__device__ __forceinline__ Chunk<double> normal_chunk(Chunk<double> *, int c, uint32_t j, uint32_t k,
+                                                      uint32_t s, uint32_t k0, uint32_t k1, int d)
+{
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(c >> 1), j, k, s), k0, k1);
+    Chunk<double> z;
+    if (c & 1)
+        box_muller(w.z, w.w, z.v[0], z.v[1]);
+    else
+        box_muller(w.x, w.y, z.v[0], z.v[1]);
+    const int i0 = 2 * c;
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+        if (i0 + e >= d) z.v[e] = 0.0;
+    return z;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bar_named(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+struct Team {
+    int tw, tthreads, team, tl, lane, wt, nteams;
+    __device__ __forceinline__ explicit Team(int team_warps)
+    {
+        tw = team_warps;
+        tthreads = 32 * tw;
+        team = threadIdx.x / tthreads;
+        tl = threadIdx.x - team * tthreads;
+        lane = threadIdx.x & 31;
+        wt = tl >> 5;
+        nteams = blockDim.x / tthreads;
+    }
+};
+
+// Sum over the threads of one team.  The xor butterfly leaves the same bits in every
+// lane (each step adds two lane values that are already equal pairwise, and addition
+// commutes); the cross-warp step reads the warp sums in warp order.  slots:
+// [nteams][2][32][NV], double-buffered so that one named barrier per call suffices.
+template <typename T, int NV>
+__device__ __forceinline__ void team_sum(T (&v)[NV], T *slots, const Team &tm, int &phase)
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (tm.tw == 1) return;
+    T *sl = slots + (size_t)((tm.team * 2 + phase) * 32) * NV;
+    if (tm.lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sl[tm.wt * NV + i] = v[i];
+    }
+    bar_named(1 + tm.team, tm.tthreads);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T a = T(0);
+        for (int w = 0; w < tm.tw; ++w) a += sl[w * NV + i];
+        v[i] = a;
+    }
+    phase ^= 1;
+}
+
+// Block-wide sum of NV doubles (all threads receive the same bits).  sm: [32][NV].
+template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV], double *sm)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[warp * NV + i] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double a = 0.0;
+        for (int w = 0; w < nw; ++w) a += sm[w * NV + i];
+        v[i] = a;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Problem table (the same formulas as documented in fbsde.h).
+// ---------------------------------------------------------------------------
+// Per-element term of the terminal feature sum; x = x0_i + Delta_i.
+template <typename Real> __device__ __forceinline__ Real g_term(int kind, Real x, Real th)
+{
+    switch (kind) {
+    case FBSDE_AC_MANUFACTURED:
+    case FBSDE_COS_LINEAR_TEST: return cos(x);
+    case FBSDE_LOGISTIC_GRAD: return x;
+    case FBSDE_HJB_LOGQUAD: return th * x * x;
+    case FBSDE_AFFINE_TEST: return th * x;
+    case FBSDE_AC_DOUBLEWELL: return x * x;
+    default: return Real(0);
+    }
+}
+
+// g from its feature sum phi.
+__device__ __forceinline__ double g_value(const Params &p, double phi)
+{
+    switch (p.kind) {
+    case FBSDE_AC_MANUFACTURED:
+    case FBSDE_COS_LINEAR_TEST: return phi / p.d;
+    case FBSDE_LOGISTIC_GRAD: return 1.0 / (1.0 + exp(-(p.T + phi / p.d)));
+    case FBSDE_HJB_LOGQUAD: return log(0.5 * (1.0 + phi));
+    case FBSDE_AFFINE_TEST: return p.A + phi;
+    case FBSDE_CUBIC_TEST: return p.A;
+    case FBSDE_AC_DOUBLEWELL: return 1.0 / (2.0 + 0.4 * phi);
+    }
+    return NAN;
+}
+
+// The y-independent part of f at time t: AC_MANUFACTURED uses phi = sum_i cos x_i,
+// the z-dependent kinds use sum_i z_i and |z|^2 of the level.
+__device__ __forceinline__ double f_feature(const Params &p, double t, double phi, double sumz,
+                                            double zz)
+{
+    switch (p.kind) {
+    case FBSDE_AC_MANUFACTURED: {
+        const double us = exp(t - p.T) * phi / p.d;
+        return us * us * us - (2.0 - 0.5 * p.sigma * p.sigma) * us;
+    }
+    case FBSDE_LOGISTIC_GRAD: return sumz;
+    case FBSDE_HJB_LOGQUAD: return zz;
+    case FBSDE_AFFINE_TEST: return p.c2 * sumz + p.c3 * t;
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double f_scalar(const Params &p, double feat, double y, double &dfdy)
+{
+    switch (p.kind) {
+    case FBSDE_AC_MANUFACTURED:
+        dfdy = 1.0 - 3.0 * y * y;
+        return y - y * y * y + feat;
+    case FBSDE_LOGISTIC_GRAD:
+        dfdy = feat;
+        return (y - (2.0 + p.d) / (2.0 * p.d)) * feat;
+    case FBSDE_HJB_LOGQUAD:
+        dfdy = 0.0;
+        return -0.5 * feat;
+    case FBSDE_AFFINE_TEST:
+        dfdy = p.c1;
+        return p.c0 + p.c1 * y + feat;
+    case FBSDE_COS_LINEAR_TEST:
+        dfdy = p.c1;
+        return p.c0 + p.c1 * y;
+    case FBSDE_CUBIC_TEST:
+    case FBSDE_AC_DOUBLEWELL:
+        dfdy = 1.0 - 3.0 * y * y;
+        return y - y * y * y;
+    }
+    dfdy = NAN;
+    return NAN;
+}
+
+// Newton iteration (2.17) on F(Y) = Y - E_hat - dt f (2.16), from Y = E_hat.
+// iters = iterations used, or -1 if newton_max_iter ran out.
+__device__ __forceinline__ double newton(const Params &p, double E_hat, double feat, int &iters)
+{
+    double y = E_hat;
+    for (int n = 1; n <= p.newton_max_iter; ++n) {
+        double dfdy;
+        const double f = f_scalar(p, feat, y, dfdy);
+        const double F = y - E_hat - p.dt * f;
+        const double dF = 1.0 - p.dt * dfdy;
+        const double dy = F / dF;
+        y -= dy;
+        if (fabs(dy) <= p.newton_tol * fmax(1.0, fabs(y))) {
+            iters = n;
+            return y;
+        }
+    }
+    iters = -1;
+    return y;
+}
+
+// Unnormalised Gaussian kernel weight exp(-(rho - rho_ref) / (h^2 rho_ref)) (Remark 2.3);
+// the shift by rho_ref = E|D|^2 cancels in the normalisation.
+__device__ __forceinline__ double kernel_weight(const Params &p, double rho, double rho_ref)
+{
+    return p.uniform ? 1.0 : exp(-(rho - rho_ref) / (p.h2 * rho_ref));
+}
+
+// ---------------------------------------------------------------------------
+// Workspace accessors.
+// ---------------------------------------------------------------------------
+template <typename Real> struct WS {
+    const Params &p;
+    __device__ __forceinline__ explicit WS(const Params &pp) : p(pp) {}
+    __device__ __forceinline__ Real *row(int s, long long j) const
+    {
+        return reinterpret_cast<Real *>(p.delta) + ((size_t)s * p.M + j) * p.ld;
+    }
+    __device__ __forceinline__ Real *w(int s) const
+    {
+        return reinterpret_cast<Real *>(p.w) + (size_t)s * p.M;
+    }
+    __device__ __forceinline__ double *Y(int s) const { return p.Y + (size_t)s * p.M; }
+    __device__ __forceinline__ Real *part(int s, int g, int v) const
+    {
+        return reinterpret_cast<Real *>(p.part) + (((size_t)s * p.G + g) * kPartVecs + v) * p.ld;
+    }
+    __device__ __forceinline__ double *spart(int s, int g) const
+    {
+        return p.spart + ((size_t)s * p.G + g) * kPartScal;
+    }
+    // FP64 vectors: 0 x, 1 r, 2 p, 3 S, 4 tA, 5 tB, 6 x0
+    __device__ __forceinline__ double *v64(int s, int which) const
+    {
+        return p.vec64 + ((size_t)s * kVec64 + which) * p.ld;
+    }
+    // stream-precision vectors: 0 p, 1 x, 2 x0; theta after all solves
+    __device__ __forceinline__ Real *vR(int s, int which) const
+    {
+        return reinterpret_cast<Real *>(p.vecR) + ((size_t)s * kVecR + which) * p.ld;
+    }
+    __device__ __forceinline__ Real *thetaR(int Q) const
+    {
+        return reinterpret_cast<Real *>(p.vecR) + (size_t)Q * kVecR * p.ld;
+    }
+};
+
+// Writes the sum over the CTA's teams of NA register accumulators as partial vectors
+// part[s][g][0..NA-1].  red: [nteams][ld] shared buffer (unused when nteams == 1).
+template <typename Real, int VPT, int NA>
+__device__ __forceinline__ void store_partials(const WS<Real> &ws, const Team &tm,
+                                               Chunk<Real> (&acc)[NA][VPT], Real *red, int s,
+                                               int g, int nch)
+{
+    constexpr int E = Chunk<Real>::E;
+    for (int a = 0; a < NA; ++a) {
+        Real *dst = ws.part(s, g, a);
+        if (tm.nteams == 1) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int c = tm.tl + tm.tthreads * v;
+                if (c < nch) st_chunk(dst + c * E, acc[a][v]);
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int c = tm.tl + tm.tthreads * v;
+                if (c < nch) st_chunk(red + (size_t)tm.team * ws.p.ld + c * E, acc[a][v]);
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+                Chunk<Real> sum = ld_chunk(red + c * E);
+                for (int t = 1; t < tm.nteams; ++t) {
+                    const Chunk<Real> o = ld_chunk(red + (size_t)t * ws.p.ld + c * E);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sum.v[e] += o.v[e];
+                }
+                st_chunk(dst + c * E, sum);
+            }
+        }
+    }
+}
+
+// Team-leader scalars (identical in every thread of a team) summed over teams in team
+// order by thread 0.  sm: [nteams][NS] doubles.
+template <int NS>
+__device__ __forceinline__ void store_scalars(double *dst, const Team &tm, const double (&v)[NS],
+                                              double *sm)
+{
+    __syncthreads();
+    if (tm.tl == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) sm[tm.team * NS + i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NS; ++i) {
+            double a = 0.0;
+            for (int t = 0; t < tm.nteams; ++t) a += sm[t * NS + i];
+            dst[i] = a;
+        }
+    }
+}
+
+__device__ __forceinline__ void row_range(long long M, int G, int g, long long &r0, long long &r1)
+{
+    r0 = (long long)((unsigned long long)M * (unsigned long long)g / (unsigned long long)G);
+    r1 = (long long)((unsigned long long)M * (unsigned long long)(g + 1) / (unsigned long long)G);
+}
+
+// Shared-memory carve-up of the streaming kernels: team slots, then the CTA reduction
+// buffer, then the scalar scratch.
+template <typename Real> struct StreamSmem {
+    Real *slots;
+    Real *red;
+    double *scal;
+    __device__ __forceinline__ StreamSmem(unsigned char *raw, const Team &tm, int ld)
+    {
+        slots = reinterpret_cast<Real *>(raw);
+        red = slots + (size_t)tm.nteams * 2 * 32 * 4;
+        double *after = reinterpret_cast<double *>(red + (tm.nteams > 1 ? (size_t)tm.nteams * ld : 0));
+        scal = after;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Forward sweep (2.7) + terminal condition + moments of the first regression (k = N-1).
+// Delta_N^j = sum_k sigma sqrt(dt) xi_{s,k,j};  Y_N^j = g(x0 + Delta_N^j);
+// w_j = K(|Delta_N^j|);  partials: S = sum w D, B = sum w (Y - yref) D and the scalars
+// sum w, sum w (Y - yref), sum w |D|^2 with yref = g(x0).
+// ---------------------------------------------------------------------------
+template <typename Real, int VPT>
+__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_forward(Params p, int Q)
+{
+    constexpr int E = Chunk<Real>::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = blockIdx.x, s = blockIdx.y;
+    const Team tm(p.team_warps);
+    const WS<Real> ws(p);
+    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
+    const int nch = p.ld / E;
+    const uint32_t sidx = p.solve0 + (uint32_t)s;
+    const Real sdt = (Real)p.sdt;
+    const Real *x0r = ws.vR(s, 2);
+    const Real *thr = ws.thetaR(Q);
+    const double yref = p.st[s].gx0;
+    const double rho_ref = p.sigma * p.sigma * p.d * p.T;
+
+    Chunk<Real> acc[2][VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        zero(acc[0][v]);
+        zero(acc[1][v]);
+    }
+    double sc[3] = {0.0, 0.0, 0.0};
+    int phase = 0;
+    long long r0, r1;
+    row_range(p.M, p.G, g, r0, r1);
+    for (long long j = r0 + tm.team; j < r1; j += tm.nteams) {
+        Chunk<Real> dl[VPT];
+        Real red2[2] = {Real(0), Real(0)};
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            zero(dl[v]);
+            if (c < nch) {
+                for (int k = 0; k < p.N; ++k) {
+                    const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
+                                                       (uint32_t)k, sidx, p.key0, p.key1, p.d);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) dl[v].v[e] += sdt * z.v[e];
+                }
+                const Chunk<Real> xc = ldg_chunk(x0r + c * E);
+                Chunk<Real> th;
+                if (p.kind == FBSDE_HJB_LOGQUAD || p.kind == FBSDE_AFFINE_TEST)
+                    th = ldg_chunk(thr + c * E);
+                else
+                    zero(th);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (c * E + e < p.d) red2[0] += g_term(p.kind, xc.v[e] + dl[v].v[e], th.v[e]);
+                    red2[1] += dl[v].v[e] * dl[v].v[e];
+                }
+            }
+        }
+        team_sum(red2, sm.slots, tm, phase);
+        const double Yj = g_value(p, (double)red2[0]);
+        const Real wr = (Real)kernel_weight(p, (double)red2[1], rho_ref);
+        const double wd = (double)wr;
+        const Real cb = (Real)(wd * (Yj - yref));
+        Real *drow = ws.row(s, j);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            if (c < nch) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    acc[0][v].v[e] += wr * dl[v].v[e];
+                    acc[1][v].v[e] += cb * dl[v].v[e];
+                }
+                st_chunk(drow + c * E, dl[v]);
+            }
+        }
+        sc[0] += wd;
+        sc[1] += wd * (Yj - yref);
+        sc[2] += wd * (double)red2[1];
+        if (tm.tl == 0) {
+            ws.Y(s)[j] = Yj;
+            ws.w(s)[j] = wr;
+        }
+    }
+    store_partials<Real, VPT, 2>(ws, tm, acc, sm.red, s, g, nch);
+    store_scalars<3>(ws.spart(s, g), tm, sc, sm.scal);
+}
+
+// ---------------------------------------------------------------------------
+// Level update (k >= 1), Eqs. (2.7), (2.9), (2.16)-(2.17), fused with the moments of
+// the next regression (level k-1):
+//   Delta_k^j = Delta_{k+1}^j - sigma sqrt(dt) xi_{s,k,j}        (in place)
+//   E_hat_j   = alpha + alpha_x . Delta_k^j                       (local affine model)
+//   Y_k^j     = Newton root of Y - E_hat_j - dt f(t_k, x0 + Delta_k^j, Y, Z_k)
+//   partials  S = sum w D, B = sum w (Y - alpha) D, scalars as in the forward sweep,
+//             w_j = K(|Delta_k^j|) with rho_ref = sigma^2 d t_k.
+// ---------------------------------------------------------------------------
+template <typename Real, int VPT>
+__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_update(Params p, int Q)
+{
+    constexpr int E = Chunk<Real>::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = blockIdx.x, s = blockIdx.y;
+    const Team tm(p.team_warps);
+    const WS<Real> ws(p);
+    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
+    const int nch = p.ld / E;
+    const int k = p.level;
+    const uint32_t sidx = p.solve0 + (uint32_t)s;
+    const Real sdt = (Real)p.sdt;
+    const Real *xr = ws.vR(s, 1);
+    const Real *x0r = ws.vR(s, 2);
+    const SolveState &st = p.st[s];
+    const double alpha = st.alpha, yref = st.alpha;
+    const double t_k = k * p.dt;
+    const double rho_ref = p.sigma * p.sigma * p.d * t_k;
+    const bool cos_feature = (p.kind == FBSDE_AC_MANUFACTURED);
+    const double feat_const = f_feature(p, t_k, 0.0, st.sumz, st.zz);
+
+    Chunk<Real> acc[2][VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        zero(acc[0][v]);
+        zero(acc[1][v]);
+    }
+    double sc[3] = {0.0, 0.0, 0.0};
+    int phase = 0, nmax = 0, nfail = 0;
+    long long r0, r1;
+    row_range(p.M, p.G, g, r0, r1);
+    for (long long j = r0 + tm.team; j < r1; j += tm.nteams) {
+        Real *drow = ws.row(s, j);
+        Chunk<Real> dl[VPT];
+        Real red3[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            if (c < nch) dl[v] = ld_chunk(drow + c * E);
+            else zero(dl[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            if (c < nch) {
+                const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
+                                                   (uint32_t)k, sidx, p.key0, p.key1, p.d);
+                const Chunk<Real> xc = ldg_chunk(xr + c * E);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    dl[v].v[e] -= sdt * z.v[e];
+                    red3[0] += xc.v[e] * dl[v].v[e];
+                    red3[1] += dl[v].v[e] * dl[v].v[e];
+                }
+                if (cos_feature) {
+                    const Chunk<Real> x0c = ldg_chunk(x0r + c * E);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (c * E + e < p.d) red3[2] += cos(x0c.v[e] + dl[v].v[e]);
+                }
+                st_chunk(drow + c * E, dl[v]);
+            }
+        }
+        team_sum(red3, sm.slots, tm, phase);
+        const double E_hat = alpha + (double)red3[0];
+        const double feat = cos_feature ? f_feature(p, t_k, (double)red3[2], 0.0, 0.0) : feat_const;
+        int it;
+        const double Yj = newton(p, E_hat, feat, it);
+        if (it < 0) ++nfail;
+        else nmax = max(nmax, it);
+        const Real wr = (Real)kernel_weight(p, (double)red3[1], rho_ref);
+        const double wd = (double)wr;
+        const Real cb = (Real)(wd * (Yj - yref));
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc[0][v].v[e] += wr * dl[v].v[e];
+                acc[1][v].v[e] += cb * dl[v].v[e];
+            }
+        }
+        sc[0] += wd;
+        sc[1] += wd * (Yj - yref);
+        sc[2] += wd * (double)red3[1];
+        if (tm.tl == 0) {
+            ws.Y(s)[j] = Yj;
+            ws.w(s)[j] = wr;
+        }
+    }
+    store_partials<Real, VPT, 2>(ws, tm, acc, sm.red, s, g, nch);
+    store_scalars<3>(ws.spart(s, g), tm, sc, sm.scal);
+    if (tm.tl == 0) {
+        if (nfail) nmax = p.newton_max_iter;
+        if (nmax) {
+            atomicMax(&p.st[s].newton_max, nmax);
+            atomicMax(&p.st[s].newton_max_all, nmax);
+        }
+        if (nfail) atomicCAS(&p.st[s].status, 0, (int)FBSDE_ERR_NEWTON);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-free product of the regression (Sec. 2.4, Steps 1 and 2) on the centred
+// operator: partial_g = sum_{j in CTA g} w_j (D_j . v) D_j with v = vR(s, 0).
+// The solve-level finalisation subtracts S (S.v), adds lambda v and normalises.
+// ---------------------------------------------------------------------------
+template <typename Real, int VPT>
+__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_matvec(Params p, int Q)
+{
+    constexpr int E = Chunk<Real>::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = blockIdx.x, s = blockIdx.y;
+    if (p.st[s].done) return;
+    const Team tm(p.team_warps);
+    const WS<Real> ws(p);
+    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
+    const int nch = p.ld / E;
+    const Real *pv = ws.vR(s, 0);
+    const Real *wv = ws.w(s);
+
+    Chunk<Real> acc[1][VPT], pc[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        zero(acc[0][v]);
+        const int c = tm.tl + tm.tthreads * v;
+        if (c < nch) pc[v] = ldg_chunk(pv + c * E);
+        else zero(pc[v]);
+    }
+    int phase = 0;
+    long long r0, r1;
+    row_range(p.M, p.G, g, r0, r1);
+    for (long long j = r0 + tm.team; j < r1; j += tm.nteams) {
+        const Real *drow = ws.row(s, j);
+        Chunk<Real> dl[VPT];
+        Real t[1] = {Real(0)};
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            if (c < nch) dl[v] = ld_chunk(drow + c * E);
+            else zero(dl[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) t[0] += dl[v].v[e] * pc[v].v[e];
+        }
+        team_sum(t, sm.slots, tm, phase);
+        const Real coef = wv[j] * t[0];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[0][v].v[e] += coef * dl[v].v[e];
+        }
+    }
+    store_partials<Real, VPT, 1>(ws, tm, acc, sm.red, s, g, nch);
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per solve: set-up of the query point.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x0, const double *theta,
+                                                       int Q)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x;
+    const WS<Real> ws(p);
+    double *x = ws.v64(s, 0), *x0v = ws.v64(s, 6);
+    Real *pR = ws.vR(s, 0), *xR = ws.vR(s, 1), *x0R = ws.vR(s, 2);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // sum cos, sum x, sum x^2, sum theta x^2 / theta x
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        const double xi = i < p.d ? x0[(size_t)s * p.d + i] : 0.0;
+        const double th = (theta && i < p.d) ? theta[i] : 0.0;
+        x0v[i] = xi;
+        x0R[i] = (Real)xi;
+        x[i] = 0.0;
+        xR[i] = Real(0);
+        pR[i] = Real(0);
+        for (int v = 1; v < kVec64 - 1; ++v) ws.v64(s, v)[i] = 0.0;
+        if (s == 0) ws.thetaR(Q)[i] = (Real)th;
+        if (i < p.d) {
+            acc[0] += cos(xi);
+            acc[1] += xi;
+            acc[2] += xi * xi;
+            acc[3] += p.kind == FBSDE_HJB_LOGQUAD ? th * xi * xi : th * xi;
+        }
+    }
+    block_sum(acc, sm);
+    if (threadIdx.x == 0) {
+        SolveState st = {};
+        double phi = 0.0;
+        switch (p.kind) {
+        case FBSDE_AC_MANUFACTURED:
+        case FBSDE_COS_LINEAR_TEST: phi = acc[0]; break;
+        case FBSDE_LOGISTIC_GRAD: phi = acc[1]; break;
+        case FBSDE_HJB_LOGQUAD:
+        case FBSDE_AFFINE_TEST: phi = acc[3]; break;
+        case FBSDE_AC_DOUBLEWELL: phi = acc[2]; break;
+        }
+        st.phi0 = acc[0];
+        st.gx0 = g_value(p, phi);
+        st.yref = st.gx0;
+        p.st[s] = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per solve: moments of the level-k regression from the CTA partials.
+//   S = sum w D / W, b' = sum w (Y - yref) D / W, c' = sum w (Y - yref) / W,
+//   lambda = ridge_rel (sum w |D|^2 / W - |S|^2) / d   (ridge of Remark 2.2),
+//   rhs = b' - c' S                                      (right side of Eq. 3.19),
+//   c = c' + yref.
+// With warm = 1 the previous level's alpha_x stays in x and vR(s,0) receives it, so
+// that the next matrix-free product gives the warm-start residual; otherwise x = 0
+// and r = p = rhs.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int warm)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x;
+    const WS<Real> ws(p);
+    SolveState &st = p.st[s];
+    double W = 0.0, Cp = 0.0, Rr = 0.0;
+    for (int g = 0; g < p.G; ++g) {
+        const double *sp = ws.spart(s, g);
+        W += sp[0];
+        Cp += sp[1];
+        Rr += sp[2];
+    }
+    const double invW = 1.0 / W, cp = Cp * invW;
+    double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
+           *B = ws.v64(s, 4);
+    Real *pR = ws.vR(s, 0);
+    double a1[2] = {0.0, 0.0};  // |S|^2, |rhs|^2 needs cp: two passes
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        double sS = 0.0, sB = 0.0;
+        for (int g = 0; g < p.G; ++g) {
+            sS += (double)ws.part(s, g, 0)[i];
+            sB += (double)ws.part(s, g, 1)[i];
+        }
+        S[i] = sS * invW;
+        B[i] = sB * invW;
+        a1[0] += S[i] * S[i];
+    }
+    block_sum(a1, sm);
+    const double lambda = p.ridge_rel * (Rr * invW - a1[0]) / p.d;
+    double a2[3] = {0.0, 0.0, 0.0};  // |rhs|^2, |r|^2, S.p
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        const double rhs = B[i] - cp * S[i];
+        B[i] = rhs;
+        a2[0] += rhs * rhs;
+        if (!warm) {
+            x[i] = 0.0;
+            r[i] = rhs;
+            pp[i] = rhs;
+            pR[i] = (Real)rhs;
+            a2[1] += rhs * rhs;
+            a2[2] += S[i] * rhs;
+        } else {
+            pR[i] = (Real)x[i];
+        }
+    }
+    block_sum(a2, sm);
+    if (threadIdx.x == 0) {
+        if (p.newton_level >= 0 && p.tr_newton)
+            p.tr_newton[(size_t)s * p.N + p.newton_level] = st.newton_max;
+        st.c = cp + st.yref;
+        st.lambda = lambda;
+        st.invW = invW;
+        st.rhs2 = a2[0];
+        st.iters = 0;
+        if (!warm) {
+            st.rr = a2[1];
+            st.sp = a2[2];
+            st.done = (a2[1] <= p.cg_tol2 * a2[0]) ? 1 : 0;
+        } else {
+            st.done = 0;  // the warm-start product must run
+        }
+    }
+}
+
+// After the product q = sum_g partial (with v = x): r = rhs - ((q/W - S (S.x)) + lambda x),
+// p = r.  (Warm start of the CG iteration from the previous level's alpha_x.)
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_cg_start(Params p)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x;
+    const WS<Real> ws(p);
+    SolveState &st = p.st[s];
+    double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
+           *rhs = ws.v64(s, 4);
+    Real *pR = ws.vR(s, 0);
+    double a0[1] = {0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) a0[0] += S[i] * x[i];
+    block_sum(a0, sm);
+    const double sx = a0[0], invW = st.invW, lambda = st.lambda;
+    double a[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        double q = 0.0;
+        for (int g = 0; g < p.G; ++g) q += (double)ws.part(s, g, 0)[i];
+        const double Ax = q * invW - S[i] * sx + lambda * x[i];
+        const double ri = rhs[i] - Ax;
+        r[i] = ri;
+        pp[i] = ri;
+        pR[i] = (Real)ri;
+        a[0] += ri * ri;
+        a[1] += S[i] * ri;
+    }
+    block_sum(a, sm);
+    if (threadIdx.x == 0) {
+        st.rr = a[0];
+        st.sp = a[1];
+        st.done = (a[0] <= p.cg_tol2 * st.rhs2) ? 1 : 0;
+    }
+}
+
+// One CG step after q_partial = sum_g w (D.p) D:
+//   q = q_partial/W - S (S.p) + lambda p,  a = rr/(p.q),  x += a p,  r -= a q,
+//   p = r + (rr'/rr) p.
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_cg_finalize(Params p)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x;
+    SolveState &st = p.st[s];
+    if (st.done) return;
+    const WS<Real> ws(p);
+    double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
+           *q = ws.v64(s, 5);
+    Real *pR = ws.vR(s, 0);
+    const double invW = st.invW, lambda = st.lambda, sp = st.sp, rr = st.rr;
+    double a[1] = {0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        double qs = 0.0;
+        for (int g = 0; g < p.G; ++g) qs += (double)ws.part(s, g, 0)[i];
+        const double qi = qs * invW - S[i] * sp + lambda * pp[i];
+        q[i] = qi;
+        a[0] += pp[i] * qi;
+    }
+    block_sum(a, sm);
+    if (!(a[0] > 0.0) || !isfinite(a[0])) {  // breakdown: keep the current iterate
+        if (threadIdx.x == 0) {
+            st.done = 1;
+            if (!(rr <= p.cg_tol2 * st.rhs2) && st.status == 0) st.status = FBSDE_ERR_CG;
+        }
+        return;
+    }
+    const double step = rr / a[0];
+    double b[1] = {0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        x[i] += step * pp[i];
+        r[i] -= step * q[i];
+        b[0] += r[i] * r[i];
+    }
+    block_sum(b, sm);
+    const double rr_new = b[0], beta = rr_new / rr;
+    double c[1] = {0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        const double pi = r[i] + beta * pp[i];
+        pp[i] = pi;
+        pR[i] = (Real)pi;
+        c[0] += S[i] * pi;
+    }
+    block_sum(c, sm);
+    if (threadIdx.x == 0) {
+        st.rr = rr_new;
+        st.sp = c[0];
+        st.iters += 1;
+        const bool conv = rr_new <= p.cg_tol2 * st.rhs2;
+        if (conv) st.done = 1;
+        else if (st.iters >= p.cg_max_iter) {
+            st.done = 1;
+            st.cg_exhausted += 1;
+            if (st.status == 0) st.status = FBSDE_ERR_CG;
+        }
+    }
+}
+
+// After the CG solve of level k: alpha = c - S . alpha_x (Eq. 3.20), Z_k = sigma alpha_x,
+// trace outputs; at k = 0 the Newton step at x0 gives u(0,x0) (Algorithm 1).
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x, k = p.level;
+    const WS<Real> ws(p);
+    SolveState &st = p.st[s];
+    const double *x = ws.v64(s, 0), *S = ws.v64(s, 3);
+    Real *xR = ws.vR(s, 1);
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        const double xi = x[i];
+        xR[i] = (Real)xi;
+        a[0] += S[i] * xi;
+        a[1] += xi;
+        a[2] += xi * xi;
+        if (i < p.d) {
+            if (p.tr_alpha_x) p.tr_alpha_x[((size_t)s * p.N + k) * p.d + i] = xi;
+            if (k == 0 && p.grad) p.grad[(size_t)s * p.d + i] = xi;
+        }
+    }
+    block_sum(a, sm);
+    if (threadIdx.x == 0) {
+        const double alpha = st.c - a[0];
+        st.alpha = alpha;
+        st.yref = alpha;
+        st.sumz = p.sigma * a[1];
+        st.zz = p.sigma * p.sigma * a[2];
+        st.newton_max = 0;
+        if (p.tr_alpha) p.tr_alpha[(size_t)s * p.N + k] = alpha;
+        if (p.tr_cg) p.tr_cg[(size_t)s * p.N + k] = st.iters;
+        if (k == 0) {
+            const double feat = f_feature(p, 0.0, st.phi0, st.sumz, st.zz);
+            int it;
+            const double u = newton(p, alpha, feat, it);
+            if (it < 0 && st.status == 0) st.status = FBSDE_ERR_NEWTON;
+            const int used = it < 0 ? p.newton_max_iter : it;
+            st.newton_max_all = max(st.newton_max_all, used);
+            if (p.tr_newton) p.tr_newton[(size_t)s * p.N] = used;
+            if (!isfinite(u) && st.status == 0) st.status = FBSDE_ERR_NONFINITE;
+            p.u0[s] = u;
+        }
+    }
+}
+
+// Trace copy of the forward-sweep end state (X_N - x0 and Y_N) into FP64 arrays.
+template <typename Real> __global__ void k_trace_forward(Params p)
+{
+    const WS<Real> ws(p);
+    const size_t total = (size_t)gridDim.y * p.M * p.d;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)p.M * p.d;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int s = blockIdx.y;
+        const long long j = idx / p.d;
+        const int i = (int)(idx - (size_t)j * p.d);
+        if (p.tr_x_N) p.tr_x_N[((size_t)s * p.M + j) * p.d + i] = (double)ws.row(s, j)[i];
+        if (i == 0 && p.tr_y_N) p.tr_y_N[(size_t)s * p.M + j] = ws.Y(s)[j];
+    }
+    (void)total;
+}
+
+template <typename Real>
+__global__ void k_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d, Real *out)
+{
+    constexpr int E = Chunk<Real>::E;
+    const int nch = (d + E - 1) / E;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nj * nch;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int jj = (int)(idx / nch), c = (int)(idx - (long long)jj * nch);
+        const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, j0 + (uint32_t)jj, k, s, k0, k1, d);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (c * E + e < d) out[(size_t)jj * d + c * E + e] = z.v[e];
+    }
+}
+
+}  // namespace dev
+}  // namespace fbsde

@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in ``include/fbsde.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libfbsde_gb300.so``.  Torch tensors supply device memory and the current
+CUDA stream.  There is no CPU fallback: if the library is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfbsde_gb300.so")
+
+FBSDE_OK, FBSDE_ERR_ARG, FBSDE_ERR_WORKSPACE, FBSDE_ERR_CUDA = 0, 1, 2, 3
+FBSDE_ERR_NEWTON, FBSDE_ERR_CG, FBSDE_ERR_TIMEOUT, FBSDE_ERR_NONFINITE = 4, 5, 6, 7
+FBSDE_FP32, FBSDE_FP64 = 0, 1
+FBSDE_MAX_D = 16384
+
+KINDS = {
+    "ac_manufactured": 0,
+    "logistic_grad": 1,
+    "hjb_logquad": 2,
+    "affine_test": 3,
+    "cubic_test": 4,
+    "ac_doublewell": 5,
+    "cos_linear_test": 6,
+}
+PRECISIONS = {"fp32": FBSDE_FP32, "fp64": FBSDE_FP64}
+
+
+class fbsde_problem(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("d", C.c_int32), ("N", C.c_int32), ("precision", C.c_int32),
+        ("M", C.c_int64), ("sigma", C.c_double), ("T", C.c_double), ("theta", C.c_void_p),
+        ("A", C.c_double), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+        ("c3", C.c_double), ("h", C.c_double), ("ridge_rel", C.c_double),
+        ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("newton_max_iter", C.c_int32),
+        ("newton_tol", C.c_double),
+    ]
+
+
+class fbsde_trace(C.Structure):
+    _fields_ = [("alpha", C.c_void_p), ("alpha_x", C.c_void_p), ("cg_iters", C.c_void_p),
+                ("newton_iters", C.c_void_p), ("x_N", C.c_void_p), ("y_N", C.c_void_p)]
+
+
+class fbsde_kernel_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("timed", C.c_int64), ("total_ms", C.c_double)]
+
+
+class fbsde_diag(C.Structure):
+    _fields_ = [("status", C.c_int32), ("solves_cg_exhausted", C.c_int32),
+                ("max_newton_iters", C.c_int32), ("reserved", C.c_int32)]
+
+
+EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
+           "fbsde_host_staging_bytes", "fbsde_diagnostics", "fbsde_philox4x32_10",
+           "fbsde_normals", "fbsde_status_string", "fbsde_abi_version",
+           "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name"]
+FBSDE_NUM_KERNELS = 9
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        lib = C.CDLL(path)
+        P, V, I32, I64, U32, U64, SZ = (C.POINTER(fbsde_problem), C.c_void_p, C.c_int32,
+                                        C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t)
+        lib.fbsde_workspace_bytes.argtypes = [P, I32]
+        lib.fbsde_workspace_bytes.restype = SZ
+        lib.fbsde_solve.argtypes = [P, I32, V, U64, U32, V, V, C.POINTER(fbsde_trace), V, SZ, V]
+        lib.fbsde_solve.restype = C.c_int
+        lib.fbsde_solve_host.argtypes = [P, I32, V, U64, U32, V, V, V, SZ, V]
+        lib.fbsde_solve_host.restype = C.c_int
+        lib.fbsde_host_staging_bytes.argtypes = [P, I32]
+        lib.fbsde_host_staging_bytes.restype = SZ
+        lib.fbsde_diagnostics.argtypes = [P, I32, V, C.POINTER(fbsde_diag), V]
+        lib.fbsde_diagnostics.restype = C.c_int
+        lib.fbsde_philox4x32_10.argtypes = [V, V, V, I64, V]
+        lib.fbsde_philox4x32_10.restype = C.c_int
+        lib.fbsde_normals.argtypes = [U64, U32, U32, U32, I32, I32, I32, V, V]
+        lib.fbsde_normals.restype = C.c_int
+        lib.fbsde_status_string.argtypes = [C.c_int]
+        lib.fbsde_status_string.restype = C.c_char_p
+        lib.fbsde_profile_start.argtypes = [I32]
+        lib.fbsde_profile_start.restype = C.c_int
+        lib.fbsde_profile_stop.argtypes = [C.POINTER(fbsde_kernel_stats)]
+        lib.fbsde_profile_stop.restype = C.c_int
+        lib.fbsde_kernel_name.argtypes = [C.c_int]
+        lib.fbsde_kernel_name.restype = C.c_char_p
+        lib.fbsde_abi_version.argtypes = []
+        lib.fbsde_abi_version.restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_problem(kind: str, d: int, N: int, M: int, sigma: float, T: float,
+                 precision: str = "fp32", theta=None, A: float = 0.0, c0: float = 0.0,
+                 c1: float = 0.0, c2: float = 0.0, c3: float = 0.0, h: float = 2.0,
+                 ridge_rel: float = 1e-3, cg_tol: float = 1e-6, cg_max_iter: int = 0,
+                 newton_max_iter: int = 0, newton_tol: float = 0.0) -> fbsde_problem:
+    """Fill the C problem struct; theta is a device tensor (or host array for the
+    host-buffer entry point) whose storage must outlive the call."""
+    return fbsde_problem(KINDS[kind], int(d), int(N), PRECISIONS[precision], int(M),
+                         float(sigma), float(T), _ptr(theta), float(A), float(c0), float(c1),
+                         float(c2), float(c3), float(h), float(ridge_rel), float(cg_tol),
+                         int(cg_max_iter), int(newton_max_iter), float(newton_tol))
+
+
+def fbsde_workspace_bytes(problem: fbsde_problem, Q: int) -> int:
+    return int(load_library().fbsde_workspace_bytes(C.byref(problem), int(Q)))
+
+
+def fbsde_host_staging_bytes(problem: fbsde_problem, Q: int) -> int:
+    return int(load_library().fbsde_host_staging_bytes(C.byref(problem), int(Q)))
+
+
+def fbsde_solve(problem: fbsde_problem, Q: int, x0, seed: int, solve_index0: int, u0,
+                grad_u0, workspace, trace: fbsde_trace | None = None, stream=None) -> int:
+    """x0 [Q, d], u0 [Q], grad_u0 [Q, d] (or None) and workspace are CUDA tensors."""
+    return int(load_library().fbsde_solve(
+        C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), C.byref(trace) if trace is not None else None, _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def fbsde_solve_host(problem: fbsde_problem, Q: int, x0: np.ndarray, seed: int,
+                     solve_index0: int, u0: np.ndarray, grad_u0: np.ndarray | None, workspace,
+                     stream=None) -> int:
+    """Host-buffer variant: x0, u0, grad_u0 (and problem.theta) are host arrays."""
+    for a in (x0, u0, grad_u0):
+        if a is not None:
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+    return int(load_library().fbsde_solve_host(
+        C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream)))
+
+
+def fbsde_diagnostics(problem: fbsde_problem, Q: int, workspace, stream=None) -> fbsde_diag:
+    out = fbsde_diag()
+    st = load_library().fbsde_diagnostics(C.byref(problem), int(Q), _ptr(workspace),
+                                          C.byref(out), _stream(stream))
+    if st != FBSDE_OK:
+        raise RuntimeError(f"fbsde_diagnostics: {fbsde_status_string(st)}")
+    return out
+
+
+def fbsde_philox4x32_10(ctr, key, out, stream=None) -> int:
+    """ctr [n, 4], key [2], out [n, 4]: uint32 data in int32 CUDA tensors."""
+    n = ctr.shape[0]
+    return int(load_library().fbsde_philox4x32_10(_ptr(ctr), _ptr(key), _ptr(out), n,
+                                                  _stream(stream)))
+
+
+def fbsde_normals(seed: int, s: int, k: int, j0: int, nj: int, d: int, precision: str, out,
+                  stream=None) -> int:
+    return int(load_library().fbsde_normals(int(seed), int(s), int(k), int(j0), int(nj),
+                                            int(d), PRECISIONS[precision], _ptr(out),
+                                            _stream(stream)))
+
+
+def fbsde_status_string(status: int) -> str:
+    return load_library().fbsde_status_string(int(status)).decode()
+
+
+def fbsde_profile_start(max_timed_launches: int) -> int:
+    return int(load_library().fbsde_profile_start(int(max_timed_launches)))
+
+
+def fbsde_profile_stop() -> dict:
+    """Per kernel family: launches, timed launches and summed event milliseconds."""
+    lib = load_library()
+    arr = (fbsde_kernel_stats * FBSDE_NUM_KERNELS)()
+    check(lib.fbsde_profile_stop(arr), "fbsde_profile_stop")
+    return {lib.fbsde_kernel_name(i).decode(): {"launches": int(arr[i].launches),
+                                                  "timed": int(arr[i].timed),
+                                                  "total_ms": float(arr[i].total_ms)}
+            for i in range(FBSDE_NUM_KERNELS)}
+
+
+def fbsde_abi_version() -> int:
+    return int(load_library().fbsde_abi_version())
+
+
+def check(status: int, what: str = "fbsde") -> None:
+    if status != FBSDE_OK:
+        raise RuntimeError(f"{what}: {fbsde_status_string(status)} ({status})")
+
+
+class Solver:
+    """Owns the device workspace for one problem shape and runs solves on it."""
+
+    def __init__(self, kind: str, d: int, N: int, M: int, sigma: float, T: float, Q: int,
+                 precision: str = "fp32", theta=None, device="cuda", **params):
+        import torch
+        self.torch = torch
+        self.Q = int(Q)
+        self.device = torch.device(device)
+        self.theta = None
+        if theta is not None:
+            self.theta = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=self.device)
+        self.problem = make_problem(kind, d, N, M, sigma, T, precision, theta=self.theta,
+                                    **params)
+        nbytes = fbsde_workspace_bytes(self.problem, self.Q)
+        if nbytes == 0:
+            raise ValueError("invalid problem parameters")
+        self.ws_bytes = nbytes
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self.workspace = self.workspace[off:off + nbytes]
+
+    def solve(self, x0, seed: int, solve_index0: int = 0, trace: bool = False,
+              trace_forward: bool = False, check_status: bool = True) -> dict:
+        torch = self.torch
+        p = self.problem
+        x0 = torch.as_tensor(x0, dtype=torch.float64, device=self.device).contiguous()
+        assert x0.shape == (self.Q, p.d)
+        u0 = torch.empty(self.Q, dtype=torch.float64, device=self.device)
+        grad = torch.empty(self.Q, p.d, dtype=torch.float64, device=self.device)
+        out = {"u0": u0, "grad": grad}
+        tr = None
+        if trace or trace_forward:
+            tr = fbsde_trace()
+        if trace:
+            out["alpha"] = torch.full((self.Q, p.N), math.nan, dtype=torch.float64,
+                                      device=self.device)
+            out["alpha_x"] = torch.full((self.Q, p.N, p.d), math.nan, dtype=torch.float64,
+                                        device=self.device)
+            out["cg_iters"] = torch.zeros(self.Q, p.N, dtype=torch.int32, device=self.device)
+            out["newton_iters"] = torch.zeros(self.Q, p.N, dtype=torch.int32, device=self.device)
+            tr.alpha, tr.alpha_x = _ptr(out["alpha"]), _ptr(out["alpha_x"])
+            tr.cg_iters, tr.newton_iters = _ptr(out["cg_iters"]), _ptr(out["newton_iters"])
+        if trace_forward:
+            out["x_N"] = torch.empty(self.Q, p.M, p.d, dtype=torch.float64, device=self.device)
+            out["y_N"] = torch.empty(self.Q, p.M, dtype=torch.float64, device=self.device)
+            tr.x_N, tr.y_N = _ptr(out["x_N"]), _ptr(out["y_N"])
+        check(fbsde_solve(p, self.Q, x0, seed, solve_index0, u0, grad, self.workspace, tr),
+              "fbsde_solve")
+        if check_status:
+            dg = fbsde_diagnostics(p, self.Q, self.workspace)
+            out["status"] = int(dg.status)
+            out["max_newton_iters"] = int(dg.max_newton_iters)
+            out["solves_cg_exhausted"] = int(dg.solves_cg_exhausted)
+        return out
