@@ -154,6 +154,32 @@ FBSDE_API int fbsde_solve_host(const fbsde_problem *P, int32_t Q, const double *
                      uint32_t solve_index0, double *u0_host, double *grad_u0_host,
                      void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
 
+/*
+ * fbsde_solve without a caller-supplied workspace, for callers that cannot allocate
+ * device memory: a host application whose allocator owns the whole device, a plugin
+ * that runs on another framework's stream and must not call cudaMalloc (which can
+ * synchronise the device), or code that must not grow its memory after start-up.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * The workspace is a fixed array of FBSDE_NOALLOC_MAX_BYTES in the library's device
+ * module.  Every GPU that loads the library holds that array until the process exits.
+ * Problems with fbsde_workspace_bytes(P, Q) > FBSDE_NOALLOC_MAX_BYTES are rejected with
+ * FBSDE_ERR_WORKSPACE before any work is enqueued.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *   x0, u0, grad_u0 and P->theta are device pointers, as for fbsde_solve; grad_u0 may
+ *   be NULL.  There is no trace output.
+ * The first call on each device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents.  Each solve
+ * rewrites every byte of it that it later reads, so nothing needs clearing between
+ * calls, but calls whose GPU work may overlap in time (other streams, other host
+ * threads) race on the array and must be serialised by the caller.
+ */
+#define FBSDE_NOALLOC_MAX_BYTES (64u << 20)
+FBSDE_API int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const double *x0,
+                                  uint64_t seed, uint32_t solve_index0, double *u0,
+                                  double *grad_u0, fbsde_stream_t stream);
+
 /* Extra workspace bytes fbsde_solve_host needs on top of fbsde_workspace_bytes. */
 FBSDE_API size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q);
 

@@ -62,7 +62,9 @@ class fbsde_diag(C.Structure):
 EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_host_staging_bytes", "fbsde_diagnostics", "fbsde_philox4x32_10",
            "fbsde_normals", "fbsde_status_string", "fbsde_abi_version",
-           "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name"]
+           "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
+           "fbsde_solve_noalloc"]
+FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 9
 
 _lock = threading.Lock()
@@ -103,6 +105,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_profile_stop.restype = C.c_int
         lib.fbsde_kernel_name.argtypes = [C.c_int]
         lib.fbsde_kernel_name.restype = C.c_char_p
+        lib.fbsde_solve_noalloc.argtypes = [P, I32, V, U64, U32, V, V, V]
+        lib.fbsde_solve_noalloc.restype = C.c_int
         lib.fbsde_abi_version.argtypes = []
         lib.fbsde_abi_version.restype = C.c_int
         _lib = lib
@@ -167,6 +171,14 @@ def fbsde_solve_host(problem: fbsde_problem, Q: int, x0: np.ndarray, seed: int,
         C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
         _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
         _stream(stream)))
+
+
+def fbsde_solve_noalloc(problem: fbsde_problem, Q: int, x0, seed: int, solve_index0: int,
+                        u0, grad_u0, stream=None) -> int:
+    """The solve on the library's built-in scratch array (no workspace argument)."""
+    return int(load_library().fbsde_solve_noalloc(
+        C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), _stream(stream)))
 
 
 def fbsde_diagnostics(problem: fbsde_problem, Q: int, workspace, stream=None) -> fbsde_diag:
