@@ -203,15 +203,17 @@ FBSDE_API int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, 
 /* Kernel families of the solve, for the profiler below. */
 typedef enum {
     FBSDE_K_SETUP = 0,      /* per-query set-up                                          */
-    FBSDE_K_FORWARD = 1,    /* forward sweep (2.7) + terminal + first moments            */
-    FBSDE_K_UPDATE = 2,     /* level update: reverse step, prediction, Newton, moments   */
+    FBSDE_K_FORWARD = 1,    /* forward sweep (2.7) of the particle rows                  */
+    FBSDE_K_UPDATE = 2,     /* level update: reverse step of the particle rows           */
     FBSDE_K_MATVEC = 3,     /* matrix-free product of the regression (Sec. 2.4, Steps 1-2)*/
-    FBSDE_K_MOMENTS = 4,    /* per-query reduction of the moments                        */
-    FBSDE_K_CG_START = 5,   /* warm-start residual                                       */
+    FBSDE_K_MOMENTS = 4,    /* weighted moments of the regression (streaming)            */
+    FBSDE_K_REDUCE = 5,     /* fixed-order FP64 sum of per-CTA partial vectors           */
     FBSDE_K_CG_STEP = 6,    /* per-query CG vector update                                */
     FBSDE_K_CG_POST = 7,    /* intercept, Z, outputs                                     */
     FBSDE_K_TRACE = 8,      /* trace copies                                              */
-    FBSDE_NUM_KERNELS = 9
+    FBSDE_K_PARTICLES = 9,  /* per-particle terminal value / prediction + Newton, weights*/
+    FBSDE_K_FINALIZE = 10,  /* per-query regression set-up from the moments              */
+    FBSDE_NUM_KERNELS = 11
 } fbsde_kernel_family;
 
 typedef struct {

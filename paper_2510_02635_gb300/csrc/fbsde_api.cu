@@ -68,6 +68,16 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.threads = L.teams * 32 * L.team_warps;
     const long long gmax = std::max<long long>(1, P->M / kMinRowsPerCta);
     L.G = (int)std::min<long long>(gmax, std::max(1, (kTargetCtas + Q - 1) / Q));
+    // row-segment kernels: one warp per 32 * seg_vpt chunks of a row
+    L.seg_vpt = nch >= 128 ? 4 : (nch >= 64 ? 2 : 1);
+    L.nseg = (nch + 32 * L.seg_vpt - 1) / (32 * L.seg_vpt);
+    L.row_blocks = (int)std::min<long long>(((long long)Q * P->M * L.nseg + 7) / 8,
+                                            (long long)kRowBlocks);
+    // per-particle kernel: 256 particles per block
+    L.GP = (int)((P->M + 255) / 256);
+    // moments: column tiles of 256 * mom_vm chunks
+    L.mom_vm = nch > 256 ? 2 : 1;
+    L.mom_tiles = (nch + 256 * L.mom_vm - 1) / (256 * L.mom_vm);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -78,8 +88,10 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_delta = take(Qs * Ms * lds * L.real_sz);
     L.off_Y = take(Qs * Ms * sizeof(double));
     L.off_w = take(Qs * Ms * L.real_sz);
+    L.off_coef = take(Qs * Ms * 3 * L.real_sz);
+    L.off_segp = take(Qs * Ms * (size_t)L.nseg * 3 * L.real_sz);
     L.off_part = take(Qs * L.G * kPartVecs * lds * L.real_sz);
-    L.off_spart = take(Qs * L.G * kPartScal * sizeof(double));
+    L.off_spart = take(Qs * L.GP * kPartScal * sizeof(double));
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
@@ -96,6 +108,10 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.ld = L.ld;
     p.N = P->N;
     p.G = L.G;
+    p.Q = L.Q;
+    p.nseg = L.nseg;
+    p.GP = L.GP;
+    p.GS = L.GP;
     p.team_warps = L.team_warps;
     p.M = P->M;
     p.sigma = P->sigma;
@@ -121,6 +137,8 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.delta = base + L.off_delta;
     p.Y = reinterpret_cast<double *>(base + L.off_Y);
     p.w = base + L.off_w;
+    p.coef = base + L.off_coef;
+    p.segp = base + L.off_segp;
     p.part = base + L.off_part;
     p.spart = reinterpret_cast<double *>(base + L.off_spart);
     p.vec64 = reinterpret_cast<double *>(base + L.off_vec64);
@@ -173,8 +191,9 @@ struct ProfScope {
     }
 };
 
-// Algorithm 1: forward sweep, then the backward levels k = N-1..0, each a regression
-// (moments, warm-started CG on the Schur complement) followed by the particle update.
+// Algorithm 1: forward sweep, then the backward levels k = N-1..0.  Each level: the CG
+// solve of its regression (moments already reduced), then, for k >= 1, the particle
+// update to level k and the moments of the level k-1 regression.
 template <typename Real>
 cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta, cudaStream_t s)
 {
@@ -185,24 +204,31 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
         ProfScope ps_(fam, s);                                                               \
         if ((e = (call)) != cudaSuccess) return e;                                           \
     } while (0)
-    FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, L.Q, s));
+    FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, s));
     FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
+    p.level = p.N;
+    FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
     if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
+    FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+    FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+    p.newton_level = -1;
+    FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 0, s));
     for (int k = p.N - 1; k >= 0; --k) {
         p.level = k;
-        p.newton_level = (k == p.N - 1) ? -1 : k + 1;
-        p.has_r = (k < p.N - 1) ? 1 : 0;  // warm start from alpha_x of level k+1
-        FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments_finalize(p, L, s));
-        if (p.has_r) {
-            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
-            FBSDE_TRY(FBSDE_K_CG_START, LR::cg_start(p, L, s));
-        }
         for (int it = 0; it < p.cg_max_iter; ++it) {
             FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_finalize(p, L, s));
+            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
         }
         FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
-        if (k >= 1) FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
+        if (k >= 1) {
+            FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
+            FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+            FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+            p.newton_level = k;
+            FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
+        }
     }
 #undef FBSDE_TRY
     return cudaSuccess;
@@ -406,9 +432,9 @@ int fbsde_profile_stop(fbsde_kernel_stats *out)
 
 const char *fbsde_kernel_name(int family)
 {
-    static const char *names[FBSDE_NUM_KERNELS] = {"setup",      "forward",  "update",
-                                                   "matvec",     "moments",  "cg_start",
-                                                   "cg_step",    "cg_post",  "trace"};
+    static const char *names[FBSDE_NUM_KERNELS] = {
+        "setup", "forward", "update", "matvec", "moments", "reduce",
+        "cg_step", "cg_post", "trace", "particles", "finalize"};
     return (family >= 0 && family < FBSDE_NUM_KERNELS) ? names[family] : "unknown";
 }
 

@@ -1,14 +1,16 @@
 // fbsde_internal.cuh -- shared declarations of the CUDA implementation (not part of the ABI).
 //
 // Data layout in HBM (one workspace, caller-allocated, 256-byte aligned sections):
-//   delta  [Q][M][ld]   Real   particle displacement X_k^j - x0 of the current level
-//   Y      [Q][M]       double Y_k^j of the current level
-//   w      [Q][M]       Real   unnormalised kernel weight of particle j for the next regression
-//   part   [Q][G][3][ld] Real  per-CTA partial d-vectors (moments S, B, R or the CG product)
-//   spart  [Q][G][4]    double per-CTA partial scalars (sum w, sum w (Y - yref), sum w rho)
-//   vec64  [Q][7][ld]   double x (= alpha_x), r, p, S, tA, tB, x0
-//   vecR   [Q][3][ld]   Real   p, x, x0 rounded to the stream precision; then theta [ld]
-//   state  [Q]          SolveState
+//   delta  [Q][M][ld]      Real   particle displacement X_k^j - x0 of the current level
+//   Y      [Q][M]          double Y_k^j of the current level
+//   w      [Q][M]          Real   kernel weight of particle j in the current regression
+//   coef   [Q][M][3]       Real   moment coefficients (w, w (Y - yref), w D.x_ws)
+//   segp   [Q][M][nseg][3] Real   per-row-segment partial sums of the row kernels
+//   part   [Q][G][3][ld]   Real   per-CTA partial d-vectors (moments or the CG product)
+//   spart  [Q][GP][4]      double per-particle-block partial scalars
+//   vec64  [Q][7][ld]      double x (= alpha_x), r, p, S, b/rhs, q/G, x0
+//   vecR   [Q][3][ld]      Real   p, x, x0 rounded to the stream precision; then theta [ld]
+//   state  [Q]             SolveState
 // ld = d rounded up to a multiple of 4 (16-byte rows for float and 32-byte rows for
 // double); the padding of every row and vector is kept at zero.
 #pragma once
@@ -28,6 +30,7 @@ constexpr int kVecR = 3;
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // 4 x 152 SMs: CTAs of one streaming pass over all solves
 constexpr int kMinRowsPerCta = 8;
+constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-stride)
 
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
@@ -36,9 +39,11 @@ struct SolveState {
 
 struct Layout {
     int Q, d, ld, N, G, precision, team_warps, vpt, teams, threads;
+    int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks;
     int64_t M;
     size_t real_sz;
-    size_t off_delta, off_Y, off_w, off_part, off_spart, off_vec64, off_vecR, off_state;
+    size_t off_delta, off_Y, off_w, off_coef, off_segp, off_part, off_spart, off_vec64, off_vecR,
+        off_state;
     size_t total;
 };
 
@@ -46,7 +51,7 @@ struct Layout {
 struct Params {
     // problem
     int kind, d, ld, N, G, team_warps, level, uniform, cg_max_iter, newton_max_iter, has_r,
-        newton_level;
+        newton_level, Q, nseg, GP, GS;
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
     uint32_t key0, key1, solve0;
@@ -54,6 +59,8 @@ struct Params {
     void *delta;
     double *Y;
     void *w;
+    void *coef;
+    void *segp;
     void *part;
     double *spart;
     double *vec64;
@@ -65,23 +72,24 @@ struct Params {
     int32_t *tr_cg, *tr_newton;
 };
 
-// Host-side launchers, one set per stream precision (defined in fbsde_kernels.cu).
+// Host-side launchers, one set per stream precision (fbsde_launch.cuh).
 template <typename Real> struct Launch {
-    static cudaError_t setup(const Params &p, const double *x0, const double *theta, int Q,
-                             cudaStream_t s);
+    static cudaError_t setup(const Params &p, const double *x0, const double *theta, cudaStream_t s);
     static cudaError_t forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t update(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t particles(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t moments(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t reduce(const Params &p, const Layout &L, int nvec, int dst0, int skip_done,
+                              cudaStream_t s);
     static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);
-    static cudaError_t moments_finalize(const Params &p, const Layout &L, cudaStream_t s);
-    static cudaError_t cg_start(const Params &p, const Layout &L, cudaStream_t s);
-    static cudaError_t cg_finalize(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t moments_finalize(const Params &p, const Layout &L, int warm, cudaStream_t s);
+    static cudaError_t cg_step(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
                                void *out, cudaStream_t st);
 };
 
-cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
-                          cudaStream_t s);
+
 
 }  // namespace fbsde

@@ -2,15 +2,18 @@
 // precision Real of the particle stream (float or double).  Included once per
 // precision by fbsde_kernels_f32.cu / fbsde_kernels_f64.cu.
 //
-// Work decomposition of the streaming kernels (forward sweep, per-level update and
-// the matrix-free product of the CG solve): grid (G, Q) with CTA (g, s) owning the
-// particle rows [M g / G, M (g+1) / G) of solve s.  A CTA holds one or more "teams"
-// of warps; a team owns one particle row at a time, each thread holding VPT 16-byte
-// chunks of it in registers (chunk c = lane_in_team + team_threads * v).  Per-row
-// sums (dot products, norms, the terminal/driver features) are reduced with a warp
-// butterfly plus, for multi-warp teams, one named barrier.  Each team accumulates its
-// d-vectors in registers; the CTA writes their sum as one partial that the
-// one-CTA-per-solve kernels reduce in a fixed order in FP64.
+// Kernel families of one solve (query points s = 0..Q-1 in one launch each):
+//   k_forward, k_update    row-segment kernels: one warp per (s, particle, segment),
+//                          Philox/Box-Muller in registers, the particle row updated in
+//                          place, per-segment partial sums written out (no barriers);
+//   k_particles            one thread per particle: segment sums, FP64 Newton, kernel
+//                          weights and the three moment coefficients;
+//   k_moments              streaming weighted column sums of the particle rows;
+//   k_matvec               the matrix-free product of the regression operator (a team
+//                          of warps per row: dot product, then the weighted row sum);
+//   k_reduce_partials      fixed-order FP64 sum of the per-CTA partial vectors;
+//   k_moments_finalize, k_cg_step, k_cg_post, k_setup
+//                          one CTA per query: FP64 d-vector algebra of the regression.
 #pragma once
 #include <math.h>
 
@@ -303,6 +306,7 @@ __device__ __forceinline__ double kernel_weight(const Params &p, double rho, dou
     return p.uniform ? 1.0 : exp(-(rho - rho_ref) / (p.h2 * rho_ref));
 }
 
+
 // ---------------------------------------------------------------------------
 // Workspace accessors.
 // ---------------------------------------------------------------------------
@@ -318,15 +322,25 @@ template <typename Real> struct WS {
         return reinterpret_cast<Real *>(p.w) + (size_t)s * p.M;
     }
     __device__ __forceinline__ double *Y(int s) const { return p.Y + (size_t)s * p.M; }
+    // per-particle moment coefficients (w, w (Y - yref), w (D . x_ws))
+    __device__ __forceinline__ Real *coef(int s, long long j) const
+    {
+        return reinterpret_cast<Real *>(p.coef) + ((size_t)s * p.M + j) * 3;
+    }
+    // per-particle, per-row-segment partial sums [3]
+    __device__ __forceinline__ Real *segp(int s, long long j, int seg) const
+    {
+        return reinterpret_cast<Real *>(p.segp) + (((size_t)s * p.M + j) * p.nseg + seg) * 3;
+    }
     __device__ __forceinline__ Real *part(int s, int g, int v) const
     {
         return reinterpret_cast<Real *>(p.part) + (((size_t)s * p.G + g) * kPartVecs + v) * p.ld;
     }
-    __device__ __forceinline__ double *spart(int s, int g) const
+    __device__ __forceinline__ double *spart(int s, int b) const
     {
-        return p.spart + ((size_t)s * p.G + g) * kPartScal;
+        return p.spart + ((size_t)s * p.GS + b) * kPartScal;
     }
-    // FP64 vectors: 0 x, 1 r, 2 p, 3 S, 4 tA, 5 tB, 6 x0
+    // FP64 vectors: 0 x (= alpha_x), 1 r, 2 p, 3 S, 4 b / rhs, 5 q or G, 6 x0
     __device__ __forceinline__ double *v64(int s, int which) const
     {
         return p.vec64 + ((size_t)s * kVec64 + which) * p.ld;
@@ -336,69 +350,11 @@ template <typename Real> struct WS {
     {
         return reinterpret_cast<Real *>(p.vecR) + ((size_t)s * kVecR + which) * p.ld;
     }
-    __device__ __forceinline__ Real *thetaR(int Q) const
+    __device__ __forceinline__ Real *thetaR() const
     {
-        return reinterpret_cast<Real *>(p.vecR) + (size_t)Q * kVecR * p.ld;
+        return reinterpret_cast<Real *>(p.vecR) + (size_t)p.Q * kVecR * p.ld;
     }
 };
-
-// Writes the sum over the CTA's teams of NA register accumulators as partial vectors
-// part[s][g][0..NA-1].  red: [nteams][ld] shared buffer (unused when nteams == 1).
-template <typename Real, int VPT, int NA>
-__device__ __forceinline__ void store_partials(const WS<Real> &ws, const Team &tm,
-                                               Chunk<Real> (&acc)[NA][VPT], Real *red, int s,
-                                               int g, int nch)
-{
-    constexpr int E = Chunk<Real>::E;
-    for (int a = 0; a < NA; ++a) {
-        Real *dst = ws.part(s, g, a);
-        if (tm.nteams == 1) {
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int c = tm.tl + tm.tthreads * v;
-                if (c < nch) st_chunk(dst + c * E, acc[a][v]);
-            }
-        } else {
-            __syncthreads();
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int c = tm.tl + tm.tthreads * v;
-                if (c < nch) st_chunk(red + (size_t)tm.team * ws.p.ld + c * E, acc[a][v]);
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-                Chunk<Real> sum = ld_chunk(red + c * E);
-                for (int t = 1; t < tm.nteams; ++t) {
-                    const Chunk<Real> o = ld_chunk(red + (size_t)t * ws.p.ld + c * E);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) sum.v[e] += o.v[e];
-                }
-                st_chunk(dst + c * E, sum);
-            }
-        }
-    }
-}
-
-// Team-leader scalars (identical in every thread of a team) summed over teams in team
-// order by thread 0.  sm: [nteams][NS] doubles.
-template <int NS>
-__device__ __forceinline__ void store_scalars(double *dst, const Team &tm, const double (&v)[NS],
-                                              double *sm)
-{
-    __syncthreads();
-    if (tm.tl == 0) {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) sm[tm.team * NS + i] = v[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) {
-            double a = 0.0;
-            for (int t = 0; t < tm.nteams; ++t) a += sm[t * NS + i];
-            dst[i] = a;
-        }
-    }
-}
 
 __device__ __forceinline__ void row_range(long long M, int G, int g, long long &r0, long long &r1)
 {
@@ -406,165 +362,115 @@ __device__ __forceinline__ void row_range(long long M, int G, int g, long long &
     r1 = (long long)((unsigned long long)M * (unsigned long long)(g + 1) / (unsigned long long)G);
 }
 
-// Shared-memory carve-up of the streaming kernels: team slots, then the CTA reduction
-// buffer, then the scalar scratch.
-template <typename Real> struct StreamSmem {
-    Real *slots;
-    Real *red;
-    double *scal;
-    __device__ __forceinline__ StreamSmem(unsigned char *raw, const Team &tm, int ld)
-    {
-        slots = reinterpret_cast<Real *>(raw);
-        red = slots + (size_t)tm.nteams * 2 * 32 * 4;
-        double *after = reinterpret_cast<double *>(red + (tm.nteams > 1 ? (size_t)tm.nteams * ld : 0));
-        scal = after;
+template <typename T, int NV> __device__ __forceinline__ void warp_sum(T (&v)[NV])
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
     }
-};
+}
 
 // ---------------------------------------------------------------------------
-// Forward sweep (2.7) + terminal condition + moments of the first regression (k = N-1).
-// Delta_N^j = sum_k sigma sqrt(dt) xi_{s,k,j};  Y_N^j = g(x0 + Delta_N^j);
-// w_j = K(|Delta_N^j|);  partials: S = sum w D, B = sum w (Y - yref) D and the scalars
-// sum w, sum w (Y - yref), sum w |D|^2 with yref = g(x0).
+// Row-segment kernels.  Work item = (query s, particle j, segment); one warp per item,
+// lane l holding chunks c0 + l + 32 v (v < VPT) of the segment.  Each item writes its
+// warp sums to segp; the per-particle kernel adds the segments in order.  No barriers,
+// no shared memory, coalesced 512-byte accesses per warp instruction.
 // ---------------------------------------------------------------------------
+
+// Forward sweep (2.7): Delta_N^j = sum_k sigma sqrt(dt) xi_{s,k,j} (X_0 = x0), stored;
+// segment sums of (|Delta|^2, terminal feature of g at x0 + Delta).
 template <typename Real, int VPT>
-__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_forward(Params p, int Q)
+__global__ void __launch_bounds__(256) k_forward(Params p)
 {
     constexpr int E = Chunk<Real>::E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = blockIdx.x, s = blockIdx.y;
-    const Team tm(p.team_warps);
     const WS<Real> ws(p);
-    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
+    const int lane = threadIdx.x & 31;
     const int nch = p.ld / E;
-    const uint32_t sidx = p.solve0 + (uint32_t)s;
+    const long long items = (long long)p.Q * p.M * p.nseg;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const Real sdt = (Real)p.sdt;
-    const Real *x0r = ws.vR(s, 2);
-    const Real *thr = ws.thetaR(Q);
-    const double yref = p.st[s].gx0;
-    const double rho_ref = p.sigma * p.sigma * p.d * p.T;
-
-    Chunk<Real> acc[2][VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        zero(acc[0][v]);
-        zero(acc[1][v]);
-    }
-    double sc[3] = {0.0, 0.0, 0.0};
-    int phase = 0;
-    long long r0, r1;
-    row_range(p.M, p.G, g, r0, r1);
-    for (long long j = r0 + tm.team; j < r1; j += tm.nteams) {
-        Chunk<Real> dl[VPT];
-        Real red2[2] = {Real(0), Real(0)};
+    const bool need_theta = p.kind == FBSDE_HJB_LOGQUAD || p.kind == FBSDE_AFFINE_TEST;
+    const Real *thr = ws.thetaR();
+    for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
+         it += nwarps) {
+        const int seg = (int)(it % p.nseg);
+        const long long row = it / p.nseg;
+        const int s = (int)(row / p.M);
+        const long long j = row - (long long)s * p.M;
+        const uint32_t sidx = p.solve0 + (uint32_t)s;
+        const Real *x0r = ws.vR(s, 2);
+        Real *drow = ws.row(s, j);
+        Real acc[2] = {Real(0), Real(0)};  // |D|^2, g feature
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int c = tm.tl + tm.tthreads * v;
-            zero(dl[v]);
+            const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) {
+                Chunk<Real> dl;
+                zero(dl);
                 for (int k = 0; k < p.N; ++k) {
                     const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
                                                        (uint32_t)k, sidx, p.key0, p.key1, p.d);
 #pragma unroll
-                    for (int e = 0; e < E; ++e) dl[v].v[e] += sdt * z.v[e];
+                    for (int e = 0; e < E; ++e) dl.v[e] += sdt * z.v[e];
                 }
                 const Chunk<Real> xc = ldg_chunk(x0r + c * E);
                 Chunk<Real> th;
-                if (p.kind == FBSDE_HJB_LOGQUAD || p.kind == FBSDE_AFFINE_TEST)
-                    th = ldg_chunk(thr + c * E);
-                else
-                    zero(th);
+                if (need_theta) th = ldg_chunk(thr + c * E);
+                else zero(th);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    if (c * E + e < p.d) red2[0] += g_term(p.kind, xc.v[e] + dl[v].v[e], th.v[e]);
-                    red2[1] += dl[v].v[e] * dl[v].v[e];
+                    acc[0] += dl.v[e] * dl.v[e];
+                    if (c * E + e < p.d) acc[1] += g_term(p.kind, xc.v[e] + dl.v[e], th.v[e]);
                 }
+                st_chunk(drow + c * E, dl);
             }
         }
-        team_sum(red2, sm.slots, tm, phase);
-        const double Yj = g_value(p, (double)red2[0]);
-        const Real wr = (Real)kernel_weight(p, (double)red2[1], rho_ref);
-        const double wd = (double)wr;
-        const Real cb = (Real)(wd * (Yj - yref));
-        Real *drow = ws.row(s, j);
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int c = tm.tl + tm.tthreads * v;
-            if (c < nch) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    acc[0][v].v[e] += wr * dl[v].v[e];
-                    acc[1][v].v[e] += cb * dl[v].v[e];
-                }
-                st_chunk(drow + c * E, dl[v]);
-            }
-        }
-        sc[0] += wd;
-        sc[1] += wd * (Yj - yref);
-        sc[2] += wd * (double)red2[1];
-        if (tm.tl == 0) {
-            ws.Y(s)[j] = Yj;
-            ws.w(s)[j] = wr;
+        warp_sum(acc);
+        if (lane == 0) {
+            Real *o = ws.segp(s, j, seg);
+            o[0] = acc[0];
+            o[1] = acc[1];
+            o[2] = Real(0);
         }
     }
-    store_partials<Real, VPT, 2>(ws, tm, acc, sm.red, s, g, nch);
-    store_scalars<3>(ws.spart(s, g), tm, sc, sm.scal);
 }
 
-// ---------------------------------------------------------------------------
-// Level update (k >= 1), Eqs. (2.7), (2.9), (2.16)-(2.17), fused with the moments of
-// the next regression (level k-1):
-//   Delta_k^j = Delta_{k+1}^j - sigma sqrt(dt) xi_{s,k,j}        (in place)
-//   E_hat_j   = alpha + alpha_x . Delta_k^j                       (local affine model)
-//   Y_k^j     = Newton root of Y - E_hat_j - dt f(t_k, x0 + Delta_k^j, Y, Z_k)
-//   partials  S = sum w D, B = sum w (Y - alpha) D, scalars as in the forward sweep,
-//             w_j = K(|Delta_k^j|) with rho_ref = sigma^2 d t_k.
-// ---------------------------------------------------------------------------
+// Level update (k >= 1): Delta_k = Delta_{k+1} - sigma sqrt(dt) xi_{s,k,j} in place (the
+// forward recursion (2.7) solved for X_k); segment sums of (alpha_x . Delta_k, |Delta_k|^2,
+// sum_i cos(x0_i + Delta_k,i) for the Allen-Cahn source).
 template <typename Real, int VPT>
-__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_update(Params p, int Q)
+__global__ void __launch_bounds__(256) k_update(Params p)
 {
     constexpr int E = Chunk<Real>::E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = blockIdx.x, s = blockIdx.y;
-    const Team tm(p.team_warps);
     const WS<Real> ws(p);
-    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
+    const int lane = threadIdx.x & 31;
     const int nch = p.ld / E;
     const int k = p.level;
-    const uint32_t sidx = p.solve0 + (uint32_t)s;
+    const long long items = (long long)p.Q * p.M * p.nseg;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const Real sdt = (Real)p.sdt;
-    const Real *xr = ws.vR(s, 1);
-    const Real *x0r = ws.vR(s, 2);
-    const SolveState &st = p.st[s];
-    const double alpha = st.alpha, yref = st.alpha;
-    const double t_k = k * p.dt;
-    const double rho_ref = p.sigma * p.sigma * p.d * t_k;
-    const bool cos_feature = (p.kind == FBSDE_AC_MANUFACTURED);
-    const double feat_const = f_feature(p, t_k, 0.0, st.sumz, st.zz);
-
-    Chunk<Real> acc[2][VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        zero(acc[0][v]);
-        zero(acc[1][v]);
-    }
-    double sc[3] = {0.0, 0.0, 0.0};
-    int phase = 0, nmax = 0, nfail = 0;
-    long long r0, r1;
-    row_range(p.M, p.G, g, r0, r1);
-    for (long long j = r0 + tm.team; j < r1; j += tm.nteams) {
+    const bool cos_feature = p.kind == FBSDE_AC_MANUFACTURED;
+    for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
+         it += nwarps) {
+        const int seg = (int)(it % p.nseg);
+        const long long row = it / p.nseg;
+        const int s = (int)(row / p.M);
+        const long long j = row - (long long)s * p.M;
+        const uint32_t sidx = p.solve0 + (uint32_t)s;
+        const Real *xr = ws.vR(s, 1);
+        const Real *x0r = ws.vR(s, 2);
         Real *drow = ws.row(s, j);
         Chunk<Real> dl[VPT];
-        Real red3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int c = tm.tl + tm.tthreads * v;
+            const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) dl[v] = ld_chunk(drow + c * E);
-            else zero(dl[v]);
         }
+        Real acc[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int c = tm.tl + tm.tthreads * v;
+            const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) {
                 const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
                                                    (uint32_t)k, sidx, p.key0, p.key1, p.d);
@@ -572,63 +478,235 @@ __global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_update(Params p, int Q
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     dl[v].v[e] -= sdt * z.v[e];
-                    red3[0] += xc.v[e] * dl[v].v[e];
-                    red3[1] += dl[v].v[e] * dl[v].v[e];
+                    acc[0] += xc.v[e] * dl[v].v[e];
+                    acc[1] += dl[v].v[e] * dl[v].v[e];
                 }
                 if (cos_feature) {
                     const Chunk<Real> x0c = ldg_chunk(x0r + c * E);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if (c * E + e < p.d) red3[2] += cos(x0c.v[e] + dl[v].v[e]);
+                        if (c * E + e < p.d) acc[2] += cos(x0c.v[e] + dl[v].v[e]);
                 }
                 st_chunk(drow + c * E, dl[v]);
             }
         }
-        team_sum(red3, sm.slots, tm, phase);
-        const double E_hat = alpha + (double)red3[0];
-        const double feat = cos_feature ? f_feature(p, t_k, (double)red3[2], 0.0, 0.0) : feat_const;
-        int it;
-        const double Yj = newton(p, E_hat, feat, it);
-        if (it < 0) ++nfail;
-        else nmax = max(nmax, it);
-        const Real wr = (Real)kernel_weight(p, (double)red3[1], rho_ref);
-        const double wd = (double)wr;
-        const Real cb = (Real)(wd * (Yj - yref));
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                acc[0][v].v[e] += wr * dl[v].v[e];
-                acc[1][v].v[e] += cb * dl[v].v[e];
-            }
-        }
-        sc[0] += wd;
-        sc[1] += wd * (Yj - yref);
-        sc[2] += wd * (double)red3[1];
-        if (tm.tl == 0) {
-            ws.Y(s)[j] = Yj;
-            ws.w(s)[j] = wr;
+        warp_sum(acc);
+        if (lane == 0) {
+            Real *o = ws.segp(s, j, seg);
+            o[0] = acc[0];
+            o[1] = acc[1];
+            o[2] = acc[2];
         }
     }
-    store_partials<Real, VPT, 2>(ws, tm, acc, sm.red, s, g, nch);
-    store_scalars<3>(ws.spart(s, g), tm, sc, sm.scal);
-    if (tm.tl == 0) {
-        if (nfail) nmax = p.newton_max_iter;
-        if (nmax) {
-            atomicMax(&p.st[s].newton_max, nmax);
-            atomicMax(&p.st[s].newton_max_all, nmax);
+}
+
+// ---------------------------------------------------------------------------
+// Per-particle scalar work, one thread per particle (grid (ceil(M/256), Q)), FP64.
+//   terminal (level = N): Y_N = g(x0 + Delta_N) (Algorithm 1), w = K(|Delta_N|),
+//                         coefficients (w, w (Y - g(x0)), 0);
+//   level k >= 1:         E_hat = alpha + alpha_x . Delta_k (local affine model), Newton
+//                         (2.16)-(2.17) for Y_k, w = K(|Delta_k|) for the level k-1
+//                         regression, coefficients (w, w (Y - alpha), w alpha_x . Delta_k).
+// Block sums of (w, w (Y - yref), w |D|^2) go to spart in thread order.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(256) k_particles(Params p)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.y;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const WS<Real> ws(p);
+    SolveState &st = p.st[s];
+    const bool terminal = p.level == p.N;
+    const double t_k = p.level * p.dt;
+    const double rho_ref = p.sigma * p.sigma * p.d * t_k;
+    const double yref = terminal ? st.gx0 : st.alpha;
+    double sums[3] = {0.0, 0.0, 0.0};
+    int it_used = 0, failed = 0;
+    if (j < p.M) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int seg = 0; seg < p.nseg; ++seg) {
+            const Real *sp = ws.segp(s, j, seg);
+            a0 += (double)sp[0];
+            a1 += (double)sp[1];
+            a2 += (double)sp[2];
         }
-        if (nfail) atomicCAS(&p.st[s].status, 0, (int)FBSDE_ERR_NEWTON);
+        double Yj, rho, dot = 0.0;
+        if (terminal) {
+            rho = a0;
+            Yj = g_value(p, a1);
+        } else {
+            dot = a0;
+            rho = a1;
+            const double feat = p.kind == FBSDE_AC_MANUFACTURED
+                                    ? f_feature(p, t_k, a2, 0.0, 0.0)
+                                    : f_feature(p, t_k, 0.0, st.sumz, st.zz);
+            int it;
+            Yj = newton(p, st.alpha + dot, feat, it);
+            if (it < 0) {
+                failed = 1;
+                it_used = p.newton_max_iter;
+            } else {
+                it_used = it;
+            }
+        }
+        const Real wr = (Real)kernel_weight(p, rho, rho_ref);
+        const double wd = (double)wr;
+        ws.Y(s)[j] = Yj;
+        ws.w(s)[j] = wr;
+        Real *cf = ws.coef(s, j);
+        cf[0] = wr;
+        cf[1] = (Real)(wd * (Yj - yref));
+        cf[2] = (Real)(wd * dot);
+        sums[0] = wd;
+        sums[1] = wd * (Yj - yref);
+        sums[2] = wd * rho;
+    }
+    block_sum(sums, sm);
+    if (threadIdx.x == 0) {
+        double *o = ws.spart(s, blockIdx.x);
+        o[0] = sums[0];
+        o[1] = sums[1];
+        o[2] = sums[2];
+    }
+    if (!terminal) {
+        int mx = it_used;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const bool any_failed = __any_sync(0xffffffffu, failed);
+        if ((threadIdx.x & 31) == 0) {
+            if (mx) {
+                atomicMax(&st.newton_max, mx);
+                atomicMax(&st.newton_max_all, mx);
+            }
+            if (any_failed) atomicCAS(&st.status, 0, (int)FBSDE_ERR_NEWTON);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weighted moments of the next regression, a streaming column sum with three weights
+// per row: partial_g = (sum w D, sum w (Y - yref) D, sum w (D . x_ws) D) over the rows
+// of CTA g.  Grid (tiles, G, Q); a tile covers 256 VM chunks of the row; threads form
+// R row groups of tpr threads (R > 1 only for narrow rows), summed in group order.
+// ---------------------------------------------------------------------------
+template <typename Real, int VM>
+__global__ void __launch_bounds__(256) k_moments(Params p)
+{
+    constexpr int E = Chunk<Real>::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x, g = blockIdx.y, s = blockIdx.z;
+    const WS<Real> ws(p);
+    const int nch = p.ld / E;
+    const int c0 = tile * 256 * VM;
+    const int tile_nch = min(nch - c0, 256 * VM);
+    const int tpr = min(256, (tile_nch + VM - 1) / VM);
+    const int R = 256 / tpr;
+    const int rg = threadIdx.x / tpr, tc = threadIdx.x - rg * tpr;
+    long long r0, r1;
+    row_range(p.M, p.G, g, r0, r1);
+    Chunk<Real> acc[3][VM];
+#pragma unroll
+    for (int v = 0; v < VM; ++v) {
+        zero(acc[0][v]);
+        zero(acc[1][v]);
+        zero(acc[2][v]);
+    }
+    if (rg < R) {
+        for (long long j = r0 + rg; j < r1; j += R) {
+            const Real *cf = ws.coef(s, j);
+            const Real w0 = cf[0], w1 = cf[1], w2 = cf[2];
+            const Real *drow = ws.row(s, j);
+#pragma unroll
+            for (int v = 0; v < VM; ++v) {
+                const int c = c0 + tc + tpr * v;
+                if (c - c0 < tile_nch) {
+                    const Chunk<Real> dl = ld_chunk(drow + c * E);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        acc[0][v].v[e] += w0 * dl.v[e];
+                        acc[1][v].v[e] += w1 * dl.v[e];
+                        acc[2][v].v[e] += w2 * dl.v[e];
+                    }
+                }
+            }
+        }
+    }
+    if (R == 1) {
+        if (rg >= R) return;  // threads beyond one row group own no chunk
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Real *dst = ws.part(s, g, a);
+#pragma unroll
+            for (int v = 0; v < VM; ++v) {
+                const int c = c0 + tc + tpr * v;
+                if (c - c0 < tile_nch) st_chunk(dst + c * E, acc[a][v]);
+            }
+        }
+        return;
+    }
+    // narrow rows: reduce the R row groups through shared memory, in group order
+    Real *red = reinterpret_cast<Real *>(smem_raw);  // [R][3][tile_nch][E]
+    if (rg < R) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int v = 0; v < VM; ++v) {
+                const int cl = tc + tpr * v;
+                if (cl < tile_nch)
+                    st_chunk(red + (((size_t)rg * 3 + a) * tile_nch + cl) * E, acc[a][v]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 3 * tile_nch; idx += blockDim.x) {
+        const int a = idx / tile_nch, cl = idx - a * tile_nch;
+        Chunk<Real> sum = ld_chunk(red + ((size_t)a * tile_nch + cl) * E);
+        for (int r = 1; r < R; ++r) {
+            const Chunk<Real> o = ld_chunk(red + (((size_t)r * 3 + a) * tile_nch + cl) * E);
+#pragma unroll
+            for (int e = 0; e < E; ++e) sum.v[e] += o.v[e];
+        }
+        st_chunk(ws.part(s, g, a) + (c0 + cl) * E, sum);
+    }
+}
+
+// Sum of the G per-CTA partials, in CTA order, in FP64: vectors 0..nvec-1 of part into
+// v64 slots dst0..dst0+nvec-1.  Grid (ceil(ld/256), Q).  skip_done: CG products of
+// converged queries are skipped.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_reduce_partials(Params p, int nvec, int dst0, int skip_done)
+{
+    const int s = blockIdx.y;
+    if (skip_done && p.st[s].done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.ld) return;
+    const WS<Real> ws(p);
+    for (int v = 0; v < nvec; ++v) {
+        const Real *src = ws.part(s, 0, v) + i;
+        const size_t stride = (size_t)kPartVecs * p.ld;
+        double acc = 0.0;
+        int g = 0;
+        for (; g + 8 <= p.G; g += 8) {
+            Real t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = src[(size_t)(g + u) * stride];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += (double)t[u];
+        }
+        for (; g < p.G; ++g) acc += (double)src[(size_t)g * stride];
+        ws.v64(s, dst0 + v)[i] = acc;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Matrix-free product of the regression (Sec. 2.4, Steps 1 and 2) on the centred
 // operator: partial_g = sum_{j in CTA g} w_j (D_j . v) D_j with v = vR(s, 0).
-// The solve-level finalisation subtracts S (S.v), adds lambda v and normalises.
+// A team of warps owns one row; per-row dot products are reduced with a warp
+// butterfly plus one named barrier.
 // ---------------------------------------------------------------------------
 template <typename Real, int VPT>
-__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_matvec(Params p, int Q)
+__global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_matvec(Params p)
 {
     constexpr int E = Chunk<Real>::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -636,15 +714,16 @@ __global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_matvec(Params p, int Q
     if (p.st[s].done) return;
     const Team tm(p.team_warps);
     const WS<Real> ws(p);
-    const StreamSmem<Real> sm(smem_raw, tm, p.ld);
     const int nch = p.ld / E;
+    Real *slots = reinterpret_cast<Real *>(smem_raw);
+    Real *red = slots + (size_t)tm.nteams * 2 * 32 * 4;
     const Real *pv = ws.vR(s, 0);
     const Real *wv = ws.w(s);
 
-    Chunk<Real> acc[1][VPT], pc[VPT];
+    Chunk<Real> acc[VPT], pc[VPT];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        zero(acc[0][v]);
+        zero(acc[v]);
         const int c = tm.tl + tm.tthreads * v;
         if (c < nch) pc[v] = ldg_chunk(pv + c * E);
         else zero(pc[v]);
@@ -667,30 +746,53 @@ __global__ void __launch_bounds__(VPT >= 8 ? 512 : 256) k_matvec(Params p, int Q
 #pragma unroll
             for (int e = 0; e < E; ++e) t[0] += dl[v].v[e] * pc[v].v[e];
         }
-        team_sum(t, sm.slots, tm, phase);
+        team_sum(t, slots, tm, phase);
         const Real coef = wv[j] * t[0];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[0][v].v[e] += coef * dl[v].v[e];
+            for (int e = 0; e < E; ++e) acc[v].v[e] += coef * dl[v].v[e];
         }
     }
-    store_partials<Real, VPT, 1>(ws, tm, acc, sm.red, s, g, nch);
+    Real *dst = ws.part(s, g, 0);
+    if (tm.nteams == 1) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int c = tm.tl + tm.tthreads * v;
+            if (c < nch) st_chunk(dst + c * E, acc[v]);
+        }
+        return;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int c = tm.tl + tm.tthreads * v;
+        if (c < nch) st_chunk(red + (size_t)tm.team * p.ld + c * E, acc[v]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        Chunk<Real> sum = ld_chunk(red + c * E);
+        for (int t2 = 1; t2 < tm.nteams; ++t2) {
+            const Chunk<Real> o = ld_chunk(red + (size_t)t2 * p.ld + c * E);
+#pragma unroll
+            for (int e = 0; e < E; ++e) sum.v[e] += o.v[e];
+        }
+        st_chunk(dst + c * E, sum);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per solve: set-up of the query point.
+// One CTA per query: set-up of the query point.
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x0, const double *theta,
-                                                       int Q)
+__global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x0, const double *theta)
 {
     __shared__ double sm[32 * 4];
     const int s = blockIdx.x;
     const WS<Real> ws(p);
     double *x = ws.v64(s, 0), *x0v = ws.v64(s, 6);
     Real *pR = ws.vR(s, 0), *xR = ws.vR(s, 1), *x0R = ws.vR(s, 2);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // sum cos, sum x, sum x^2, sum theta x^2 / theta x
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // sum cos, sum x, sum x^2, theta-weighted sum
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = i < p.d ? x0[(size_t)s * p.d + i] : 0.0;
         const double th = (theta && i < p.d) ? theta[i] : 0.0;
@@ -700,7 +802,7 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
         xR[i] = Real(0);
         pR[i] = Real(0);
         for (int v = 1; v < kVec64 - 1; ++v) ws.v64(s, v)[i] = 0.0;
-        if (s == 0) ws.thetaR(Q)[i] = (Real)th;
+        if (s == 0) ws.thetaR()[i] = (Real)th;
         if (i < p.d) {
             acc[0] += cos(xi);
             acc[1] += xi;
@@ -728,14 +830,12 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per solve: moments of the level-k regression from the CTA partials.
+// One CTA per query: the level-k regression from the reduced moments.
 //   S = sum w D / W, b' = sum w (Y - yref) D / W, c' = sum w (Y - yref) / W,
-//   lambda = ridge_rel (sum w |D|^2 / W - |S|^2) / d   (ridge of Remark 2.2),
-//   rhs = b' - c' S                                      (right side of Eq. 3.19),
-//   c = c' + yref.
-// With warm = 1 the previous level's alpha_x stays in x and vR(s,0) receives it, so
-// that the next matrix-free product gives the warm-start residual; otherwise x = 0
-// and r = p = rhs.
+//   lambda = ridge_rel (sum w |D|^2 / W - |S|^2) / d            (ridge of Remark 2.2)
+//   rhs = b' - c' S                                              (right side of Eq. 3.19)
+//   Gamma_c x = sum w (D . x) D / W - S (S . x)  (x = previous level's alpha_x, or 0)
+//   r = p = rhs - Gamma_c x - lambda x,  c = c' + yref.
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int warm)
@@ -745,44 +845,39 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     const WS<Real> ws(p);
     SolveState &st = p.st[s];
     double W = 0.0, Cp = 0.0, Rr = 0.0;
-    for (int g = 0; g < p.G; ++g) {
-        const double *sp = ws.spart(s, g);
+    for (int b = 0; b < p.GP; ++b) {
+        const double *sp = ws.spart(s, b);
         W += sp[0];
         Cp += sp[1];
         Rr += sp[2];
     }
     const double invW = 1.0 / W, cp = Cp * invW;
     double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
-           *B = ws.v64(s, 4);
+           *B = ws.v64(s, 4), *Gx = ws.v64(s, 5);
     Real *pR = ws.vR(s, 0);
-    double a1[2] = {0.0, 0.0};  // |S|^2, |rhs|^2 needs cp: two passes
+    double a1[2] = {0.0, 0.0};  // |S|^2, S.x
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        double sS = 0.0, sB = 0.0;
-        for (int g = 0; g < p.G; ++g) {
-            sS += (double)ws.part(s, g, 0)[i];
-            sB += (double)ws.part(s, g, 1)[i];
-        }
-        S[i] = sS * invW;
-        B[i] = sB * invW;
+        S[i] *= invW;
+        B[i] *= invW;
+        Gx[i] *= invW;
+        if (!warm) x[i] = 0.0;
         a1[0] += S[i] * S[i];
+        a1[1] += S[i] * x[i];
     }
     block_sum(a1, sm);
     const double lambda = p.ridge_rel * (Rr * invW - a1[0]) / p.d;
-    double a2[3] = {0.0, 0.0, 0.0};  // |rhs|^2, |r|^2, S.p
+    const double sx = a1[1];
+    double a2[3] = {0.0, 0.0, 0.0};  // |rhs|^2, |r|^2, S.r
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double rhs = B[i] - cp * S[i];
+        const double ri = rhs - (Gx[i] - S[i] * sx) - lambda * x[i];
         B[i] = rhs;
+        r[i] = ri;
+        pp[i] = ri;
+        pR[i] = (Real)ri;
         a2[0] += rhs * rhs;
-        if (!warm) {
-            x[i] = 0.0;
-            r[i] = rhs;
-            pp[i] = rhs;
-            pR[i] = (Real)rhs;
-            a2[1] += rhs * rhs;
-            a2[2] += S[i] * rhs;
-        } else {
-            pR[i] = (Real)x[i];
-        }
+        a2[1] += ri * ri;
+        a2[2] += S[i] * ri;
     }
     block_sum(a2, sm);
     if (threadIdx.x == 0) {
@@ -792,58 +887,18 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
         st.lambda = lambda;
         st.invW = invW;
         st.rhs2 = a2[0];
+        st.rr = a2[1];
+        st.sp = a2[2];
         st.iters = 0;
-        if (!warm) {
-            st.rr = a2[1];
-            st.sp = a2[2];
-            st.done = (a2[1] <= p.cg_tol2 * a2[0]) ? 1 : 0;
-        } else {
-            st.done = 0;  // the warm-start product must run
-        }
+        st.done = (a2[1] <= p.cg_tol2 * a2[0]) ? 1 : 0;
     }
 }
 
-// After the product q = sum_g partial (with v = x): r = rhs - ((q/W - S (S.x)) + lambda x),
-// p = r.  (Warm start of the CG iteration from the previous level's alpha_x.)
-template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_cg_start(Params p)
-{
-    __shared__ double sm[32 * 4];
-    const int s = blockIdx.x;
-    const WS<Real> ws(p);
-    SolveState &st = p.st[s];
-    double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
-           *rhs = ws.v64(s, 4);
-    Real *pR = ws.vR(s, 0);
-    double a0[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) a0[0] += S[i] * x[i];
-    block_sum(a0, sm);
-    const double sx = a0[0], invW = st.invW, lambda = st.lambda;
-    double a[2] = {0.0, 0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        double q = 0.0;
-        for (int g = 0; g < p.G; ++g) q += (double)ws.part(s, g, 0)[i];
-        const double Ax = q * invW - S[i] * sx + lambda * x[i];
-        const double ri = rhs[i] - Ax;
-        r[i] = ri;
-        pp[i] = ri;
-        pR[i] = (Real)ri;
-        a[0] += ri * ri;
-        a[1] += S[i] * ri;
-    }
-    block_sum(a, sm);
-    if (threadIdx.x == 0) {
-        st.rr = a[0];
-        st.sp = a[1];
-        st.done = (a[0] <= p.cg_tol2 * st.rhs2) ? 1 : 0;
-    }
-}
-
-// One CG step after q_partial = sum_g w (D.p) D:
-//   q = q_partial/W - S (S.p) + lambda p,  a = rr/(p.q),  x += a p,  r -= a q,
+// One CG step after q_sum = sum_g partial (FP64, slot 5):
+//   q = q_sum/W - S (S.p) + lambda p,  a = rr/(p.q),  x += a p,  r -= a q,
 //   p = r + (rr'/rr) p.
 template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_cg_finalize(Params p)
+__global__ void __launch_bounds__(kFinThreads) k_cg_step(Params p)
 {
     __shared__ double sm[32 * 4];
     const int s = blockIdx.x;
@@ -856,9 +911,7 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_finalize(Params p)
     const double invW = st.invW, lambda = st.lambda, sp = st.sp, rr = st.rr;
     double a[1] = {0.0};
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        double qs = 0.0;
-        for (int g = 0; g < p.G; ++g) qs += (double)ws.part(s, g, 0)[i];
-        const double qi = qs * invW - S[i] * sp + lambda * pp[i];
+        const double qi = q[i] * invW - S[i] * sp + lambda * pp[i];
         q[i] = qi;
         a[0] += pp[i] * qi;
     }
@@ -952,16 +1005,14 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
 template <typename Real> __global__ void k_trace_forward(Params p)
 {
     const WS<Real> ws(p);
-    const size_t total = (size_t)gridDim.y * p.M * p.d;
+    const int s = blockIdx.y;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)p.M * p.d;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const int s = blockIdx.y;
         const long long j = idx / p.d;
         const int i = (int)(idx - (size_t)j * p.d);
         if (p.tr_x_N) p.tr_x_N[((size_t)s * p.M + j) * p.d + i] = (double)ws.row(s, j)[i];
         if (i == 0 && p.tr_y_N) p.tr_y_N[(size_t)s * p.M + j] = ws.Y(s)[j];
     }
-    (void)total;
 }
 
 template <typename Real>

@@ -4,80 +4,108 @@
 
 namespace fbsde {
 
-// Dynamic shared memory of a streaming kernel: team slots, the CTA reduction buffer
-// (multi-team CTAs only) and per-team scalars.
-template <typename Real> inline size_t stream_smem(const Layout &L)
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes)
 {
-    size_t b = (size_t)L.teams * 2 * 32 * 4 * sizeof(Real);
-    if (L.teams > 1) b += (size_t)L.teams * L.ld * sizeof(Real);
-    b += (size_t)L.teams * 3 * sizeof(double) + 16;
-    return b;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-
-template <typename Real, int VPT, typename K>
-static cudaError_t launch_stream(K kernel, const Params &p, const Layout &L, cudaStream_t s)
-{
-    const size_t smem = stream_smem<Real>(L);
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    kernel<<<dim3(L.G, L.Q), L.threads, smem, s>>>(p, L.Q);
-    return cudaGetLastError();
-}
-
-#define FBSDE_VPT_DISPATCH(KERNEL)                                                        \
-    switch (L.vpt) {                                                                      \
-    case 1: return launch_stream<Real, 1>(dev::KERNEL<Real, 1>, p, L, s);                 \
-    case 2: return launch_stream<Real, 2>(dev::KERNEL<Real, 2>, p, L, s);                 \
-    case 4: return launch_stream<Real, 4>(dev::KERNEL<Real, 4>, p, L, s);                 \
-    case 8: return launch_stream<Real, 8>(dev::KERNEL<Real, 8>, p, L, s);                 \
-    }                                                                                     \
-    return cudaErrorInvalidValue;
 
 template <typename Real>
-cudaError_t Launch<Real>::setup(const Params &p, const double *x0, const double *theta, int Q,
+cudaError_t Launch<Real>::setup(const Params &p, const double *x0, const double *theta,
                                 cudaStream_t s)
 {
-    dev::k_setup<Real><<<Q, kFinThreads, 0, s>>>(p, x0, theta, Q);
+    dev::k_setup<Real><<<p.Q, kFinThreads, 0, s>>>(p, x0, theta);
     return cudaGetLastError();
 }
+
+#define FBSDE_SEG_DISPATCH(KERNEL)                                                        \
+    switch (L.seg_vpt) {                                                                  \
+    case 1: dev::KERNEL<Real, 1><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
+    case 2: dev::KERNEL<Real, 2><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
+    case 4: dev::KERNEL<Real, 4><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
+    default: return cudaErrorInvalidValue;                                                \
+    }                                                                                     \
+    return cudaGetLastError();
 
 template <typename Real>
 cudaError_t Launch<Real>::forward(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_VPT_DISPATCH(k_forward)
+    FBSDE_SEG_DISPATCH(k_forward)
 }
 
 template <typename Real>
 cudaError_t Launch<Real>::update(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_VPT_DISPATCH(k_update)
+    FBSDE_SEG_DISPATCH(k_update)
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::particles(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_particles<Real><<<dim3(L.GP, L.Q), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::moments(const Params &p, const Layout &L, cudaStream_t s)
+{
+    const dim3 grid(L.mom_tiles, L.G, L.Q);
+    const size_t smem = (size_t)3 * 256 * L.mom_vm * 16;
+    cudaError_t e;
+    if (L.mom_vm == 1) {
+        if ((e = set_smem(dev::k_moments<Real, 1>, smem)) != cudaSuccess) return e;
+        dev::k_moments<Real, 1><<<grid, 256, smem, s>>>(p);
+    } else {
+        if ((e = set_smem(dev::k_moments<Real, 2>, smem)) != cudaSuccess) return e;
+        dev::k_moments<Real, 2><<<grid, 256, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::reduce(const Params &p, const Layout &L, int nvec, int dst0,
+                                 int skip_done, cudaStream_t s)
+{
+    dev::k_reduce_partials<Real><<<dim3((L.ld + 255) / 256, L.Q), 256, 0, s>>>(p, nvec, dst0,
+                                                                              skip_done);
+    return cudaGetLastError();
+}
+
+template <typename Real, int VPT>
+static cudaError_t launch_matvec(const Params &p, const Layout &L, cudaStream_t s)
+{
+    size_t smem = (size_t)L.teams * 2 * 32 * 4 * sizeof(Real);
+    if (L.teams > 1) smem += (size_t)L.teams * L.ld * sizeof(Real);
+    cudaError_t e = set_smem(dev::k_matvec<Real, VPT>, smem);
+    if (e != cudaSuccess) return e;
+    dev::k_matvec<Real, VPT><<<dim3(L.G, L.Q), L.threads, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t Launch<Real>::matvec(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_VPT_DISPATCH(k_matvec)
+    switch (L.vpt) {
+    case 1: return launch_matvec<Real, 1>(p, L, s);
+    case 2: return launch_matvec<Real, 2>(p, L, s);
+    case 4: return launch_matvec<Real, 4>(p, L, s);
+    case 8: return launch_matvec<Real, 8>(p, L, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename Real>
-cudaError_t Launch<Real>::moments_finalize(const Params &p, const Layout &L, cudaStream_t s)
+cudaError_t Launch<Real>::moments_finalize(const Params &p, const Layout &L, int warm,
+                                           cudaStream_t s)
 {
-    dev::k_moments_finalize<Real><<<L.Q, kFinThreads, 0, s>>>(p, p.has_r);
+    dev::k_moments_finalize<Real><<<L.Q, kFinThreads, 0, s>>>(p, warm);
     return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t Launch<Real>::cg_start(const Params &p, const Layout &L, cudaStream_t s)
+cudaError_t Launch<Real>::cg_step(const Params &p, const Layout &L, cudaStream_t s)
 {
-    dev::k_cg_start<Real><<<L.Q, kFinThreads, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <typename Real>
-cudaError_t Launch<Real>::cg_finalize(const Params &p, const Layout &L, cudaStream_t s)
-{
-    dev::k_cg_finalize<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    dev::k_cg_step<Real><<<L.Q, kFinThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

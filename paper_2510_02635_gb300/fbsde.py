@@ -65,7 +65,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
            "fbsde_solve_noalloc"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
-FBSDE_NUM_KERNELS = 9
+FBSDE_NUM_KERNELS = 11
 
 _lock = threading.Lock()
 _lib = None
