@@ -75,6 +75,19 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
                                             (long long)kRowBlocks);
     // per-particle kernel: 256 particles per block
     L.GP = (int)((P->M + 255) / 256);
+    // matrix-free product: ring of mv_stages stages of mv_rows rows (~32 KB per stage,
+    // ~200 KB of shared memory in total)
+    {
+        const size_t row_bytes = (size_t)L.ld * L.real_sz;
+        const size_t stage_target = 32 * 1024, ring_target = 200 * 1024;
+        long long R = std::max<long long>(1, (long long)(stage_target / row_bytes));
+        R = std::max<long long>(L.teams, R / L.teams * L.teams);
+        L.mv_rows = (int)R;
+        L.mv_stages = (int)std::min<long long>(8, std::max<long long>(2, ring_target / (R * row_bytes)));
+        L.mv_smem = (size_t)L.mv_stages * R * row_bytes + 2 * L.mv_stages * sizeof(uint64_t) +
+                    (size_t)L.teams * 2 * 32 * L.real_sz;
+        if (L.mv_smem > 227 * 1024) return FBSDE_ERR_ARG;
+    }
     // moments: column tiles of 256 * mom_vm chunks
     L.mom_vm = nch > 256 ? 2 : 1;
     L.mom_tiles = (nch + 256 * L.mom_vm - 1) / (256 * L.mom_vm);
@@ -112,6 +125,8 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.nseg = L.nseg;
     p.GP = L.GP;
     p.GS = L.GP;
+    p.mv_rows = L.mv_rows;
+    p.mv_stages = L.mv_stages;
     p.team_warps = L.team_warps;
     p.M = P->M;
     p.sigma = P->sigma;

@@ -39,7 +39,8 @@ struct SolveState {
 
 struct Layout {
     int Q, d, ld, N, G, precision, team_warps, vpt, teams, threads;
-    int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks;
+    int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks, mv_rows, mv_stages;
+    size_t mv_smem;
     int64_t M;
     size_t real_sz;
     size_t off_delta, off_Y, off_w, off_coef, off_segp, off_part, off_spart, off_vec64, off_vecR,
@@ -51,7 +52,7 @@ struct Layout {
 struct Params {
     // problem
     int kind, d, ld, N, G, team_warps, level, uniform, cg_max_iter, newton_max_iter, has_r,
-        newton_level, Q, nseg, GP, GS;
+        newton_level, Q, nseg, GP, GS, mv_rows, mv_stages;
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
     uint32_t key0, key1, solve0;

@@ -71,25 +71,26 @@ cudaError_t Launch<Real>::reduce(const Params &p, const Layout &L, int nvec, int
     return cudaGetLastError();
 }
 
-template <typename Real, int VPT>
+template <typename Real, int VPT, bool WIDE>
 static cudaError_t launch_matvec(const Params &p, const Layout &L, cudaStream_t s)
 {
-    size_t smem = (size_t)L.teams * 2 * 32 * 4 * sizeof(Real);
-    if (L.teams > 1) smem += (size_t)L.teams * L.ld * sizeof(Real);
-    cudaError_t e = set_smem(dev::k_matvec<Real, VPT>, smem);
+    cudaError_t e = set_smem(dev::k_matvec<Real, VPT, WIDE>, L.mv_smem);
     if (e != cudaSuccess) return e;
-    dev::k_matvec<Real, VPT><<<dim3(L.G, L.Q), L.threads, smem, s>>>(p);
+    dev::k_matvec<Real, VPT, WIDE>
+        <<<dim3(L.G, L.Q), 32 * (1 + L.teams * L.team_warps), L.mv_smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t Launch<Real>::matvec(const Params &p, const Layout &L, cudaStream_t s)
 {
+    const bool wide = 32 * (1 + L.teams * L.team_warps) > 352;
     switch (L.vpt) {
-    case 1: return launch_matvec<Real, 1>(p, L, s);
-    case 2: return launch_matvec<Real, 2>(p, L, s);
-    case 4: return launch_matvec<Real, 4>(p, L, s);
-    case 8: return launch_matvec<Real, 8>(p, L, s);
+    case 1: return launch_matvec<Real, 1, false>(p, L, s);
+    case 2: return launch_matvec<Real, 2, false>(p, L, s);
+    case 4: return launch_matvec<Real, 4, false>(p, L, s);
+    case 8: return wide ? launch_matvec<Real, 8, true>(p, L, s)
+                        : launch_matvec<Real, 8, false>(p, L, s);
     }
     return cudaErrorInvalidValue;
 }
