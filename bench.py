@@ -36,6 +36,24 @@ METRIC = "particle-dim updates/sec (K*M*d per step)"
 UNIT = "particle-dim updates/s"
 
 
+def _matvec_traffic(w: W.Workload) -> float | None:
+    """DRAM bytes of one product launch of this workload, scaled from the ncu capture in
+    profiles/matvec_traffic.txt; None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "matvec_traffic.txt")
+    try:
+        lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    kv = {ln[0]: ln[1:] for ln in lines}
+    src = os.path.join(ROOT, kv["kernel_source"][2])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != kv["kernel_source"][1]:
+        return None
+    ctas = w.Q * min(max(1, w.M // 8), -(-608 // w.Q))   # CTAs of one product launch
+    return (float(kv["read_bytes_per_particle_dim"][0]) * w.Q * w.M * w.d
+            + float(kv["write_bytes_per_cta"][0]) * ctas)
+
+
 def _peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -282,7 +300,9 @@ def run_gpu(args, rank: int, world: int) -> None:
             "gpu_launches_per_step": launches / args.steps,
             "roofline": {"kernel": "matvec", "bound": "hbm", "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": _matvec_traffic(w),
+                         "traffic_source": "ncu capture at Q=4, M=4096 scaled per particle-dim "
+                                           "and per CTA (profiles/matvec_traffic.txt)",
                          "algorithmic_bytes_per_product": bytes_per_product,
                          "products_per_step": products,
                          "kernel_ms_per_step": mv_ms_step},

@@ -287,3 +287,42 @@ class Solver:
             out["max_newton_iters"] = int(dg.max_newton_iters)
             out["solves_cg_exhausted"] = int(dg.solves_cg_exhausted)
         return out
+
+
+def _main(argv=None) -> None:
+    """One solve of a seeded synthetic problem (used for profiling small cases)."""
+    import argparse
+    import time
+
+    import torch
+
+    ap = argparse.ArgumentParser(description="one fbsde_solve on cuda:0")
+    ap.add_argument("--kind", default="ac_manufactured", choices=sorted(KINDS))
+    ap.add_argument("--d", type=int, default=10000)
+    ap.add_argument("--M", type=int, default=4096)
+    ap.add_argument("--N", type=int, default=3)
+    ap.add_argument("--Q", type=int, default=4)
+    ap.add_argument("--T", type=float, default=1.0)
+    ap.add_argument("--sigma", type=float, default=1.0)
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--cg-tol", type=float, default=1e-6)
+    ap.add_argument("--cg-max-iter", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+    rng = np.random.default_rng(a.seed)
+    x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)), device="cuda")
+    theta = rng.uniform(0.5, 1.5, size=a.d) if a.kind in ("hjb_logquad", "affine_test") else None
+    solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
+                    theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
+    for r in range(a.repeat):
+        t0 = time.perf_counter()
+        out = solver.solve(x0, seed=a.seed)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
+              f"u0[0]={float(out['u0'][0]):.12f}")
+
+
+if __name__ == "__main__":
+    _main()
