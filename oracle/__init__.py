@@ -99,6 +99,14 @@ def _load():
                                       C.c_int32, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp,
                                       _dp]
             lib.orc_solve.restype = C.c_int
+            lib.orc_adjoint.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, _dp,
+                                        _dp, _dp]
+            lib.orc_adjoint.restype = C.c_int
+            lib.orc_g_grad.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+            lib.orc_g_grad.restype = None
+            lib.orc_f_grads.argtypes = [C.POINTER(_Problem), C.c_double, _dp, C.c_double, _dp,
+                                        _dp, _dp]
+            lib.orc_f_grads.restype = None
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = C.c_int
             _lib = lib
@@ -253,3 +261,34 @@ def solve(prob: Problem, x0, seed: int, solve_index: int = 0, max_levels: int | 
     if keep_levels_y:
         out.update(Y_levels=y_lv)
     return out
+
+
+def g_grad(prob: Problem, x) -> tuple[np.ndarray, np.ndarray]:
+    """(dg/dx, dg/dtheta) of the terminal condition at x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    gx, gt = np.zeros(prob.d), np.zeros(prob.d)
+    ps = prob.c_struct()
+    _load().orc_g_grad(C.byref(ps), _ptr(x), _ptr(gx), _ptr(gt))
+    return gx, gt
+
+
+def f_grads(prob: Problem, t: float, x, y: float, z) -> tuple[np.ndarray, np.ndarray]:
+    """(df/dx, df/dz) of the driver at (t, x, y, z)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    fx, fz = np.zeros(prob.d), np.zeros(prob.d)
+    ps = prob.c_struct()
+    _load().orc_f_grads(C.byref(ps), t, _ptr(x), y, _ptr(z), _ptr(fx), _ptr(fz))
+    return fx, fz
+
+
+def adjoint(prob: Problem, x0, seed: int, solve_index: int = 0) -> dict:
+    """Reverse-mode derivatives of the estimator u(0,x0) with respect to x0 and theta for
+    the same random increments (a plain tape over the levels of Algorithm 1)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    u0 = C.c_double(math.nan)
+    dx, dth = np.zeros(prob.d), np.zeros(prob.d)
+    ps = prob.c_struct()
+    st = _load().orc_adjoint(C.byref(ps), _ptr(x0), int(seed), int(solve_index), C.byref(u0),
+                             _ptr(dx), _ptr(dth))
+    return {"u0": float(u0.value), "du_dx0": dx, "du_dtheta": dth, "status": int(st)}

@@ -565,6 +565,274 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
     return status;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Derivatives of the problem table used by the adjoint.                      */
+/* ------------------------------------------------------------------------- */
+
+/* gx[i] = dg/dx_i at x; gtheta[i] = dg/dtheta_i (zero for kinds without theta). */
+void orc_g_grad(const orc_problem *P, const double *x, double *gx, double *gtheta)
+{
+    const int d = P->d;
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) gx[i] = gtheta[i] = 0.0;
+    switch (P->kind) {
+    case ORC_AC_MANUFACTURED:
+    case ORC_COS_LINEAR_TEST:
+        for (int i = 0; i < d; ++i) gx[i] = -sin(x[i]) / d;
+        break;
+    case ORC_LOGISTIC_GRAD: {
+        const double g = orc_g(P, x);
+        for (int i = 0; i < d; ++i) gx[i] = g * (1.0 - g) / d;
+        break;
+    }
+    case ORC_HJB_LOGQUAD:
+        for (int i = 0; i < d; ++i) s += P->theta[i] * x[i] * x[i];
+        for (int i = 0; i < d; ++i) {
+            gx[i] = 2.0 * P->theta[i] * x[i] / (1.0 + s);
+            gtheta[i] = x[i] * x[i] / (1.0 + s);
+        }
+        break;
+    case ORC_AFFINE_TEST:
+        for (int i = 0; i < d; ++i) {
+            gx[i] = P->theta[i];
+            gtheta[i] = x[i];
+        }
+        break;
+    case ORC_AC_DOUBLEWELL: {
+        const double g = orc_g(P, x);
+        for (int i = 0; i < d; ++i) gx[i] = -0.8 * x[i] * g * g;
+        break;
+    }
+    }
+}
+
+/* fx[i] = df/dx_i and fz[i] = df/dz_i at (t, x, y, z). */
+void orc_f_grads(const orc_problem *P, double t, const double *x, double y, const double *z,
+                 double *fx, double *fz)
+{
+    const int d = P->d;
+    for (int i = 0; i < d; ++i) fx[i] = fz[i] = 0.0;
+    switch (P->kind) {
+    case ORC_AC_MANUFACTURED: {
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) s += cos(x[i]);
+        const double e = exp(t - P->T), us = e * s / d;
+        const double dq = 3.0 * us * us - (2.0 - 0.5 * P->sigma * P->sigma);
+        for (int i = 0; i < d; ++i) fx[i] = dq * (-e * sin(x[i]) / d);
+        break;
+    }
+    case ORC_LOGISTIC_GRAD:
+        for (int i = 0; i < d; ++i) fz[i] = y - (2.0 + d) / (2.0 * d);
+        break;
+    case ORC_HJB_LOGQUAD:
+        for (int i = 0; i < d; ++i) fz[i] = -z[i];
+        break;
+    case ORC_AFFINE_TEST:
+        for (int i = 0; i < d; ++i) fz[i] = P->c2;
+        break;
+    }
+}
+
+/* CG on (Gamma_c + lambda I) v = rhs with the stored cloud D, normalised weights w and
+   first moment S (the operator of Eq. 3.19 with the ridge). */
+static int gamma_c_solve(int d, int64_t M, const double *D, const double *w, const double *S,
+                         double lambda, const double *rhs, double tol, int max_iter, double *v,
+                         double *t)
+{
+    double *r = (double *)malloc(sizeof(double) * 3 * (size_t)d);
+    if (!r) return ORC_ERR_NOMEM;
+    double *p = r + d, *q = r + 2 * d;
+    for (int i = 0; i < d; ++i) {
+        v[i] = 0.0;
+        r[i] = p[i] = rhs[i];
+    }
+    double rr = dotd(d, r, r);
+    const double stop = tol * sqrt(rr);
+    int it = 0, status = ORC_OK;
+    while (sqrt(rr) > stop) {
+        if (it >= max_iter) {
+            status = ORC_ERR_CG;
+            break;
+        }
+        gamma_c_apply(d, M, D, w, S, lambda, p, t, q);
+        const double a = rr / dotd(d, p, q);
+        for (int i = 0; i < d; ++i) {
+            v[i] += a * p[i];
+            r[i] -= a * q[i];
+        }
+        const double rr_new = dotd(d, r, r);
+        const double beta = rr_new / rr;
+        for (int i = 0; i < d; ++i) p[i] = r[i] + beta * p[i];
+        rr = rr_new;
+        ++it;
+    }
+    free(r);
+    return status;
+}
+
+/*
+ * Reverse-mode derivative of the estimator u(0,x0) of Algorithm 1 with respect to x0
+ * and to theta (the terminal coefficients), for the same random increments.  A plain
+ * tape: the forward pass stores X_k for every level, the weights, the first moments,
+ * the ridge and Y_k with F'(Y_k); the reverse pass runs k = 0..N-1:
+ *   gamma_j   = Ybar_k^j / F'_j                      (implicit function of (2.16))
+ *   alphabar  = sum_j gamma_j,
+ *   alphaxbar = sum_j gamma_j (X_k^j - x0) + sigma Zbar,  Zbar = dt sum_j gamma_j f_z
+ *   x0bar    += dt sum_j gamma_j f_x(t_k, X_k^j)
+ *   v         = (Gamma_c + lambda I)^-1 (alphaxbar - alphabar S_k)      (Eqs. 3.19-3.20)
+ *   Ybar_{k+1}^j = w_j (alphabar + (D_j - S_k) . v),  D_j = X_{k+1}^j - x0,
+ * then x0bar += sum_j Ybar_N^j grad g(X_N^j), thetabar = sum_j Ybar_N^j d_theta g(X_N^j).
+ * The kernel weights and the ridge depend only on D_j, which does not move with x0.
+ * Outputs u0, du_dx0[d], du_dtheta[d] (may be NULL).
+ */
+int orc_adjoint(const orc_problem *P, const double *x0, uint64_t seed, uint32_t solve_index,
+                double *u0, double *du_dx0, double *du_dtheta)
+{
+    const int d = P->d, N = P->N;
+    const int64_t M = P->M;
+    if (d < 1 || N < 1 || M < 2 || !(P->T > 0.0) || !(P->sigma > 0.0)) return ORC_ERR_ARG;
+    if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta) return ORC_ERR_ARG;
+    const double dt = P->T / N, sdt = P->sigma * sqrt(dt);
+    const size_t Md = (size_t)M * d;
+    double *X = (double *)malloc(sizeof(double) * Md * (N + 1));     /* X_k, k = 0..N */
+    double *Yl = (double *)malloc(sizeof(double) * (size_t)M * (N + 1)); /* Y_k        */
+    double *Fp = (double *)malloc(sizeof(double) * (size_t)M * (N + 1)); /* F'(Y_k)    */
+    double *W = (double *)malloc(sizeof(double) * (size_t)M * N);        /* w of level k */
+    double *Sl = (double *)malloc(sizeof(double) * (size_t)d * N);       /* S of level k */
+    double *AX = (double *)malloc(sizeof(double) * (size_t)d * N);       /* alpha_x      */
+    double *lam = (double *)malloc(sizeof(double) * N);
+    double *D = (double *)malloc(sizeof(double) * Md);
+    double *tmpM = (double *)malloc(sizeof(double) * M);
+    double *Yb = (double *)malloc(sizeof(double) * M);
+    double *gam = (double *)malloc(sizeof(double) * M);
+    double *vec = (double *)malloc(sizeof(double) * 8 * (size_t)d);
+    int *nit = (int *)malloc(sizeof(int) * M);
+    int status = ORC_OK;
+    if (!X || !Yl || !Fp || !W || !Sl || !AX || !lam || !D || !tmpM || !Yb || !gam || !vec || !nit) {
+        status = ORC_ERR_NOMEM;
+        goto done;
+    }
+    double *z = vec, *ab = vec + d, *rhs = vec + 2 * d, *v = vec + 3 * d, *fx = vec + 4 * d,
+           *fz = vec + 5 * d, *xb = vec + 6 * d, *tb = vec + 7 * d;
+
+    /* ---- forward sweep (2.7), stored for every level */
+#pragma omp parallel
+    {
+        double *xi = (double *)malloc(sizeof(double) * d);
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < M; ++j) {
+            for (int i = 0; i < d; ++i) X[j * (int64_t)d + i] = x0[i];
+            for (int k = 0; k < N; ++k) {
+                const double *Xk = X + (size_t)k * Md + j * (int64_t)d;
+                double *Xn = X + (size_t)(k + 1) * Md + j * (int64_t)d;
+                orc_normals(seed, solve_index, (uint32_t)k, (uint32_t)j, d, xi);
+                for (int i = 0; i < d; ++i) Xn[i] = Xk[i] + sdt * xi[i];
+            }
+            Yl[(size_t)N * M + j] = orc_g(P, X + (size_t)N * Md + j * (int64_t)d);
+        }
+        free(xi);
+    }
+    /* ---- backward sweep (Algorithm 1), recording the tape */
+    for (int k = N - 1; k >= 0; --k) {
+        const double t_k = k * dt;
+        const double *Xn = X + (size_t)(k + 1) * Md, *Xk = X + (size_t)k * Md;
+        for (size_t e = 0; e < Md; ++e) D[e] = Xn[e] - x0[e % d];
+        double alpha;
+        int it;
+        int st = orc_llr(d, M, D, Yl + (size_t)(k + 1) * M, P->sigma * P->sigma * d * (k + 1) * dt,
+                         P->h, P->ridge_rel, P->cg_tol, P->cg_max_iter, &alpha, AX + (size_t)k * d,
+                         W + (size_t)k * M, &it);
+        if (st == ORC_ERR_NOMEM || st == ORC_ERR_ARG) {
+            status = st;
+            goto done;
+        }
+        if (st != ORC_OK && status == ORC_OK) status = st;
+        /* S_k and lambda_k of this regression (as inside orc_llr) */
+        double *S = Sl + (size_t)k * d;
+        weighted_row_sum(d, M, D, W + (size_t)k * M, S);
+        double wrho = 0.0;
+        for (int64_t j = 0; j < M; ++j) {
+            double rho = 0.0;
+            for (int i = 0; i < d; ++i) rho += D[j * (int64_t)d + i] * D[j * (int64_t)d + i];
+            wrho += W[(size_t)k * M + j] * rho;
+        }
+        lam[k] = P->ridge_rel * (wrho - dotd(d, S, S)) / d;
+        const double *ax = AX + (size_t)k * d;
+        for (int i = 0; i < d; ++i) z[i] = P->sigma * ax[i];
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < M; ++j) {
+            const double *xj = Xk + j * (int64_t)d;
+            double pred = alpha;
+            for (int i = 0; i < d; ++i) pred += ax[i] * (xj[i] - x0[i]);
+            const double feat = orc_f_feature(P, t_k, xj, z);
+            const double y = orc_newton(P, pred, dt, feat, &nit[j]);
+            double dfdy;
+            (void)orc_f_scalar(P, feat, y, &dfdy);
+            Yl[(size_t)k * M + j] = y;
+            Fp[(size_t)k * M + j] = 1.0 - dt * dfdy;
+        }
+        for (int64_t j = 0; j < M; ++j)
+            if (nit[j] < 0 && status == ORC_OK) status = ORC_ERR_NEWTON;
+    }
+    {
+        double s = 0.0;
+        for (int64_t j = 0; j < M; ++j) s += Yl[j];
+        if (u0) *u0 = s / M;
+    }
+    /* ---- reverse sweep */
+    for (int i = 0; i < d; ++i) xb[i] = tb[i] = 0.0;
+    for (int64_t j = 0; j < M; ++j) Yb[j] = 1.0 / M; /* u = (1/M) sum_j Y_0^j */
+    for (int k = 0; k < N; ++k) {
+        const double t_k = k * dt;
+        const double *Xk = X + (size_t)k * Md, *Xn = X + (size_t)(k + 1) * Md;
+        const double *ax = AX + (size_t)k * d, *S = Sl + (size_t)k * d;
+        for (int i = 0; i < d; ++i) z[i] = P->sigma * ax[i];
+        double abar = 0.0;
+        for (int64_t j = 0; j < M; ++j) {
+            gam[j] = Yb[j] / Fp[(size_t)k * M + j];
+            abar += gam[j];
+        }
+        for (int i = 0; i < d; ++i) ab[i] = 0.0;
+        for (int64_t j = 0; j < M; ++j) {
+            const double *xj = Xk + j * (int64_t)d;
+            orc_f_grads(P, t_k, xj, Yl[(size_t)k * M + j], z, fx, fz);
+            for (int i = 0; i < d; ++i) {
+                ab[i] += gam[j] * (xj[i] - x0[i]) + P->sigma * dt * gam[j] * fz[i];
+                xb[i] += dt * gam[j] * fx[i];
+            }
+        }
+        for (int i = 0; i < d; ++i) rhs[i] = ab[i] - abar * S[i];
+        for (size_t e = 0; e < Md; ++e) D[e] = Xn[e] - x0[e % d];
+        int st = gamma_c_solve(d, M, D, W + (size_t)k * M, S, lam[k], rhs, P->cg_tol,
+                               P->cg_max_iter, v, tmpM);
+        if (st == ORC_ERR_NOMEM) {
+            status = st;
+            goto done;
+        }
+        if (st != ORC_OK && status == ORC_OK) status = st;
+        const double sv = dotd(d, S, v);
+        for (int64_t j = 0; j < M; ++j) {
+            double dv = 0.0;
+            for (int i = 0; i < d; ++i) dv += D[j * (int64_t)d + i] * v[i];
+            Yb[j] = W[(size_t)k * M + j] * (abar + dv - sv);
+        }
+    }
+    /* terminal condition Y_N = g(X_N) */
+    for (int64_t j = 0; j < M; ++j) {
+        orc_g_grad(P, X + (size_t)N * Md + j * (int64_t)d, fx, fz);
+        for (int i = 0; i < d; ++i) {
+            xb[i] += Yb[j] * fx[i];
+            tb[i] += Yb[j] * fz[i];
+        }
+    }
+    if (du_dx0) memcpy(du_dx0, xb, sizeof(double) * d);
+    if (du_dtheta) memcpy(du_dtheta, tb, sizeof(double) * d);
+done:
+    free(X); free(Yl); free(Fp); free(W); free(Sl); free(AX); free(lam); free(D); free(tmpM);
+    free(Yb); free(gam); free(vec); free(nit);
+    return status;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP
