@@ -180,6 +180,31 @@ FBSDE_API int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const doubl
                                   uint64_t seed, uint32_t solve_index0, double *u0,
                                   double *grad_u0, fbsde_stream_t stream);
 
+/* Bytes of device workspace that fbsde_adjoint needs (the solve's workspace plus a tape
+   of N (M + 2 d) values per query).  0 when the arguments are invalid. */
+FBSDE_API size_t fbsde_adjoint_workspace_bytes(const fbsde_problem *P, int32_t Q);
+
+/*
+ * Derivative of the estimator u(0, x0) of Algorithm 1 with respect to the query points
+ * and to theta, for the same random increments (seed, solve indices), by a reverse sweep
+ * over the levels.  The solve is re-run with a tape of its per-level regressions
+ * (weights, first moments, ridge, alpha, alpha_x, Y_k); the reverse sweep regenerates
+ * the particle paths from the Philox streams instead of storing them.  Per level it
+ * needs one extra solve with the same SPD operator as the regression (Lemma 3.7).
+ *   u0_bar    device [Q]    dL/du0 of each query (the cotangent)
+ *   u0        device [Q]    output: u(0, x0) (the re-run solve)
+ *   grad_u0   device [Q][d] output: alpha_x of level 0 (the method's grad u), or NULL
+ *   x0_bar    device [Q][d] output: u0_bar_q * d u(0, x0_q) / d x0_q
+ *   theta_bar device [d]    output: sum_q u0_bar_q * d u(0, x0_q) / d theta, or NULL;
+ *                           only for HJB_LOGQUAD and AFFINE_TEST
+ *   workspace device, >= fbsde_adjoint_workspace_bytes(P, Q) bytes, 256-byte aligned
+ * Asynchronous like fbsde_solve; device errors via fbsde_diagnostics.
+ */
+FBSDE_API int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                            uint32_t solve_index0, const double *u0_bar, double *u0,
+                            double *grad_u0, double *x0_bar, double *theta_bar, void *workspace,
+                            size_t workspace_bytes, fbsde_stream_t stream);
+
 /* Extra workspace bytes fbsde_solve_host needs on top of fbsde_workspace_bytes. */
 FBSDE_API size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q);
 
@@ -213,7 +238,8 @@ typedef enum {
     FBSDE_K_TRACE = 8,      /* trace copies                                              */
     FBSDE_K_PARTICLES = 9,  /* per-particle terminal value / prediction + Newton, weights*/
     FBSDE_K_FINALIZE = 10,  /* per-query regression set-up from the moments              */
-    FBSDE_NUM_KERNELS = 11
+    FBSDE_K_ADJOINT = 11,   /* reverse-sweep kernels other than the shared ones above    */
+    FBSDE_NUM_KERNELS = 12
 } fbsde_kernel_family;
 
 typedef struct {

@@ -109,6 +109,13 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
     L.total = off;
+    // reverse sweep: tape of the primal plus three adjoint vectors per query
+    L.off_tape_w = take((size_t)P->N * Qs * Ms * L.real_sz);
+    L.off_tape_Y = take((size_t)(P->N + 1) * Qs * Ms * sizeof(double));
+    L.off_tape_v = take(Qs * (size_t)P->N * 2 * lds * sizeof(double));
+    L.off_tape_s = take(Qs * (size_t)P->N * 4 * sizeof(double));
+    L.off_adj_v = take(Qs * 3 * lds * sizeof(double));
+    L.total_adjoint = off;
     return FBSDE_OK;
 }
 
@@ -145,6 +152,8 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.cg_max_iter = P->cg_max_iter > 0 ? P->cg_max_iter : 200;
     p.newton_max_iter = P->newton_max_iter > 0 ? P->newton_max_iter : 50;
     p.newton_tol = P->newton_tol > 0.0 ? P->newton_tol : 1e-13;
+    p.walk = -1;
+    p.theta = P->theta;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
     p.solve0 = solve0;
@@ -249,6 +258,67 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
     return cudaSuccess;
 }
 
+// Reverse sweep (see fbsde_adjoint.cuh): the primal is re-run with its tape recorded,
+// then for k = 0..N-1 the adjoint solve of level k, the per-particle adjoint and the
+// column sums, walking the particle rows forward from Delta_1 by regenerating the
+// increments.
+template <typename Real>
+cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const double *theta,
+                        const double *ubar, double *x0bar, double *thetabar, char *base,
+                        cudaStream_t s)
+{
+    using LR = Launch<Real>;
+    cudaError_t e;
+    p.tape_w = base + L.off_tape_w;
+    p.tape_Y = reinterpret_cast<double *>(base + L.off_tape_Y);
+    p.tape_v = reinterpret_cast<double *>(base + L.off_tape_v);
+    p.tape_s = reinterpret_cast<double *>(base + L.off_tape_s);
+    p.adj_v = reinterpret_cast<double *>(base + L.off_adj_v);
+    if ((e = run<Real>(p, L, x0, theta, s)) != cudaSuccess) return e;
+#define FBSDE_TRY(fam, call)                                                                 \
+    do {                                                                                     \
+        ProfScope ps_(fam, s);                                                               \
+        if ((e = (call)) != cudaSuccess) return e;                                           \
+    } while (0)
+    FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_init(p, L, ubar, s));
+    int mode_b = 0, mode_c = 0;  // terminal column functions per kind
+    switch (p.kind) {
+    case FBSDE_AC_MANUFACTURED:
+    case FBSDE_COS_LINEAR_TEST: mode_b = 1; break;
+    case FBSDE_HJB_LOGQUAD: mode_b = 2; mode_c = 1; break;
+    case FBSDE_AFFINE_TEST: mode_c = 2; break;
+    case FBSDE_AC_DOUBLEWELL: mode_b = 2; break;
+    }
+    for (int k = 0; k < p.N; ++k) {
+        p.level = k;
+        p.w = reinterpret_cast<Real *>(p.tape_w) + (size_t)k * L.Q * L.M;  // weights of level k
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_setup(p, L, s));
+        for (int it = 0; it < p.cg_max_iter; ++it) {
+            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
+        }
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_post(p, L, s));
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_rows(p, L, s));
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_zlevel(p, L, s));
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_particles(p, L, s));
+        const bool terminal = k + 1 == p.N;
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_colsum(p, L, terminal ? mode_b : (p.kind == FBSDE_AC_MANUFACTURED ? 1 : 0),
+                                                  terminal ? mode_c : 0, s));
+        FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_finalize(p, L, s));
+        if (!terminal) {  // rows Delta_{k+1} -> Delta_{k+2}, regenerating increment k+1
+            Params q = p;
+            q.level = k + 1;
+            q.walk = +1;
+            FBSDE_TRY(FBSDE_K_UPDATE, LR::update(q, L, s));
+        }
+    }
+    FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_output(p, L, x0bar, thetabar, s));
+#undef FBSDE_TRY
+    return cudaSuccess;
+}
+
 int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double *theta,
                uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
                const fbsde_trace *trace, void *workspace, size_t workspace_bytes,
@@ -302,6 +372,38 @@ int fbsde_solve(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t se
 {
     return solve_impl(P, Q, x0, P ? P->theta : nullptr, seed, solve_index0, u0, grad_u0, trace,
                       workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t fbsde_adjoint_workspace_bytes(const fbsde_problem *P, int32_t Q)
+{
+    Layout L;
+    return make_layout(P, Q, L) == FBSDE_OK ? L.total_adjoint : 0;
+}
+
+int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                  uint32_t solve_index0, const double *u0_bar, double *u0, double *grad_u0,
+                  double *x0_bar, double *theta_bar, void *workspace, size_t workspace_bytes,
+                  fbsde_stream_t stream)
+{
+    Layout L;
+    int st = check_problem(P, Q, true);
+    if (st != FBSDE_OK) return st;
+    st = make_layout(P, Q, L);
+    if (st != FBSDE_OK) return st;
+    if (!x0 || !u0_bar || !u0 || !x0_bar) return FBSDE_ERR_ARG;
+    if (theta_bar && !(P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST))
+        return FBSDE_ERR_ARG;
+    if (!workspace || workspace_bytes < L.total_adjoint ||
+        (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+        return FBSDE_ERR_WORKSPACE;
+    const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, nullptr);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    const cudaError_t e =
+        P->precision == FBSDE_FP32
+            ? run_adjoint<float>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, s)
+            : run_adjoint<double>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, s);
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
 }
 
 size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q)
@@ -449,7 +551,7 @@ const char *fbsde_kernel_name(int family)
 {
     static const char *names[FBSDE_NUM_KERNELS] = {
         "setup", "forward", "update", "matvec", "moments", "reduce",
-        "cg_step", "cg_post", "trace", "particles", "finalize"};
+        "cg_step", "cg_post", "trace", "particles", "finalize", "adjoint"};
     return (family >= 0 && family < FBSDE_NUM_KERNELS) ? names[family] : "unknown";
 }
 

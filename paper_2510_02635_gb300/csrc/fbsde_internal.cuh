@@ -34,11 +34,13 @@ constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-st
 
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
+    double abar, sv, sumz_l, zz_l;  // reverse sweep
     int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all;
 };
 
 struct Layout {
     int Q, d, ld, N, G, precision, team_warps, vpt, teams, threads;
+    size_t off_tape_w, off_tape_Y, off_tape_v, off_tape_s, off_adj_v, total_adjoint;
     int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks, mv_rows, mv_stages;
     size_t mv_smem;
     int64_t M;
@@ -52,7 +54,7 @@ struct Layout {
 struct Params {
     // problem
     int kind, d, ld, N, G, team_warps, level, uniform, cg_max_iter, newton_max_iter, has_r,
-        newton_level, Q, nseg, GP, GS, mv_rows, mv_stages;
+        newton_level, Q, nseg, GP, GS, mv_rows, mv_stages, walk;
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
     uint32_t key0, key1, solve0;
@@ -67,6 +69,10 @@ struct Params {
     double *vec64;
     void *vecR;
     SolveState *st;
+    // tape of the primal for the reverse sweep (null when not recording)
+    void *tape_w;
+    double *tape_Y, *tape_v, *tape_s, *adj_v;
+    const double *theta;
     // outputs
     double *u0, *grad;
     double *tr_alpha, *tr_alpha_x, *tr_x_N, *tr_y_N;
@@ -89,6 +95,18 @@ template <typename Real> struct Launch {
     static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
                                void *out, cudaStream_t st);
+    // reverse sweep
+    static cudaError_t adj_init(const Params &p, const Layout &L, const double *ubar, cudaStream_t s);
+    static cudaError_t adj_setup(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_post(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_rows(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_zlevel(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_particles(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_colsum(const Params &p, const Layout &L, int mode_b, int mode_c,
+                                  cudaStream_t s);
+    static cudaError_t adj_finalize(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_output(const Params &p, const Layout &L, double *x0bar, double *thetabar,
+                                  cudaStream_t s);
 };
 
 

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
     const int k = p.level;
     const long long items = (long long)p.Q * p.M * p.nseg;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const Real sdt = (Real)p.sdt;
+    const Real wsdt = (Real)(p.walk * p.sdt);  // walk = -1: X_k from X_{k+1}; +1: forward
     const bool cos_feature = p.kind == FBSDE_AC_MANUFACTURED;
     for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
          it += nwarps) {
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
                 const Chunk<Real> xc = ldg_chunk(xr + c * E);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    dl[v].v[e] -= sdt * z.v[e];
+                    dl[v].v[e] += wsdt * z.v[e];
                     acc[0] += xc.v[e] * dl[v].v[e];
                     acc[1] += dl[v].v[e] * dl[v].v[e];
                 }
@@ -636,6 +636,10 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
         const double wd = (double)wr;
         ws.Y(s)[j] = Yj;
         ws.w(s)[j] = wr;
+        if (p.tape_w) {  // record Y_level and the weights of regression level-1
+            p.tape_Y[((size_t)p.level * p.Q + s) * p.M + j] = Yj;
+            reinterpret_cast<Real *>(p.tape_w)[((size_t)(p.level - 1) * p.Q + s) * p.M + j] = wr;
+        }
         Real *cf = ws.coef(s, j);
         cf[0] = wr;
         cf[1] = (Real)(wd * (Yj - yref));
@@ -1025,6 +1029,10 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
         a2[1] += ri * ri;
         a2[2] += S[i] * ri;
     }
+    if (p.tape_v) {
+        double *tS = p.tape_v + (((size_t)s * p.N + (p.level - 1)) * 2 + 0) * p.ld;
+        for (int i = threadIdx.x; i < p.ld; i += blockDim.x) tS[i] = S[i];
+    }
     block_sum(a2, sm);
     if (threadIdx.x == 0) {
         if (p.newton_level >= 0 && p.tr_newton)
@@ -1032,6 +1040,11 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
         st.c = cp + st.yref;
         st.lambda = lambda;
         st.invW = invW;
+        if (p.tape_s) {
+            double *ts = p.tape_s + ((size_t)s * p.N + (p.level - 1)) * 4;
+            ts[0] = lambda;
+            ts[1] = invW;
+        }
         st.rhs2 = a2[0];
         st.rr = a2[1];
         st.sp = a2[2];
@@ -1122,6 +1135,7 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
             if (p.tr_alpha_x) p.tr_alpha_x[((size_t)s * p.N + k) * p.d + i] = xi;
             if (k == 0 && p.grad) p.grad[(size_t)s * p.d + i] = xi;
         }
+        if (p.tape_v) p.tape_v[(((size_t)s * p.N + k) * 2 + 1) * p.ld + i] = xi;
     }
     block_sum(a, sm);
     if (threadIdx.x == 0) {
@@ -1132,6 +1146,7 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
         st.zz = p.sigma * p.sigma * a[2];
         st.newton_max = 0;
         if (p.tr_alpha) p.tr_alpha[(size_t)s * p.N + k] = alpha;
+        if (p.tape_s) p.tape_s[((size_t)s * p.N + k) * 4 + 2] = alpha;
         if (p.tr_cg) p.tr_cg[(size_t)s * p.N + k] = st.iters;
         if (k == 0) {
             const double feat = f_feature(p, 0.0, st.phi0, st.sumz, st.zz);

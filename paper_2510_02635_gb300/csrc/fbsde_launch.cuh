@@ -1,5 +1,6 @@
 // fbsde_launch.cuh -- host launchers of the kernels for one stream precision.
 #pragma once
+#include "fbsde_adjoint.cuh"
 #include "fbsde_kernels.cuh"
 
 namespace fbsde {
@@ -132,6 +133,79 @@ cudaError_t Launch<Real>::normals(uint64_t seed, uint32_t sidx, uint32_t k, uint
 {
     dev::k_normals<Real><<<1024, 256, 0, st>>>(seed, sidx, k, j0, nj, d,
                                                 reinterpret_cast<Real *>(out));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_init(const Params &p, const Layout &L, const double *ubar, cudaStream_t s)
+{
+    dev::k_adj_init<Real><<<L.Q, kFinThreads, 0, s>>>(p, ubar);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_setup(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_adj_setup<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_post(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_adj_post<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_rows(const Params &p, const Layout &L, cudaStream_t s)
+{
+    FBSDE_SEG_DISPATCH(k_adj_rows)
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_zlevel(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_adj_zlevel<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_particles(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_adj_particles<Real><<<dim3(L.GP, L.Q), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_colsum(const Params &p, const Layout &L, int mode_b, int mode_c,
+                                     cudaStream_t s)
+{
+    const dim3 grid(L.mom_tiles, L.G, L.Q);
+    const size_t smem = (size_t)3 * 256 * L.mom_vm * 16;
+    cudaError_t e;
+    if (L.mom_vm == 1) {
+        if ((e = set_smem(dev::k_adj_colsum<Real, 1>, smem)) != cudaSuccess) return e;
+        dev::k_adj_colsum<Real, 1><<<grid, 256, smem, s>>>(p, mode_b, mode_c);
+    } else {
+        if ((e = set_smem(dev::k_adj_colsum<Real, 2>, smem)) != cudaSuccess) return e;
+        dev::k_adj_colsum<Real, 2><<<grid, 256, smem, s>>>(p, mode_b, mode_c);
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_finalize(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_adj_finalize<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_output(const Params &p, const Layout &L, double *x0bar,
+                                     double *thetabar, cudaStream_t s)
+{
+    dev::k_adj_output<Real><<<64, 256, 0, s>>>(p, x0bar, thetabar);
     return cudaGetLastError();
 }
 

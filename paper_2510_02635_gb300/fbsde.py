@@ -63,9 +63,9 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_host_staging_bytes", "fbsde_diagnostics", "fbsde_philox4x32_10",
            "fbsde_normals", "fbsde_status_string", "fbsde_abi_version",
            "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
-           "fbsde_solve_noalloc"]
+           "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
-FBSDE_NUM_KERNELS = 11
+FBSDE_NUM_KERNELS = 12
 
 _lock = threading.Lock()
 _lib = None
@@ -107,6 +107,10 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_kernel_name.restype = C.c_char_p
         lib.fbsde_solve_noalloc.argtypes = [P, I32, V, U64, U32, V, V, V]
         lib.fbsde_solve_noalloc.restype = C.c_int
+        lib.fbsde_adjoint_workspace_bytes.argtypes = [P, I32]
+        lib.fbsde_adjoint_workspace_bytes.restype = SZ
+        lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
+        lib.fbsde_adjoint.restype = C.c_int
         lib.fbsde_abi_version.argtypes = []
         lib.fbsde_abi_version.restype = C.c_int
         _lib = lib
@@ -179,6 +183,19 @@ def fbsde_solve_noalloc(problem: fbsde_problem, Q: int, x0, seed: int, solve_ind
     return int(load_library().fbsde_solve_noalloc(
         C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
         _ptr(grad_u0), _stream(stream)))
+
+
+def fbsde_adjoint_workspace_bytes(problem: fbsde_problem, Q: int) -> int:
+    return int(load_library().fbsde_adjoint_workspace_bytes(C.byref(problem), int(Q)))
+
+
+def fbsde_adjoint(problem: fbsde_problem, Q: int, x0, seed: int, solve_index0: int, u0_bar,
+                  u0, grad_u0, x0_bar, theta_bar, workspace, stream=None) -> int:
+    """Reverse sweep: x0_bar = u0_bar du/dx0, theta_bar = sum_q u0_bar_q du_q/dtheta."""
+    return int(load_library().fbsde_adjoint(
+        C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0_bar),
+        _ptr(u0), _ptr(grad_u0), _ptr(x0_bar), _ptr(theta_bar), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def fbsde_diagnostics(problem: fbsde_problem, Q: int, workspace, stream=None) -> fbsde_diag:
@@ -254,6 +271,32 @@ class Solver:
         off = (-self.workspace.data_ptr()) % 256
         self.workspace = self.workspace[off:off + nbytes]
 
+    def _adjoint_workspace(self):
+        if getattr(self, "adj_workspace", None) is None:
+            n = fbsde_adjoint_workspace_bytes(self.problem, self.Q)
+            self.adj_workspace = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        return self.adj_workspace
+
+    def adjoint(self, x0, seed: int, u0_bar=None, solve_index0: int = 0,
+                with_theta: bool = False, check_status: bool = True) -> dict:
+        """u(0,x0), grad u (method), and the reverse-sweep derivatives du/dx0, du/dtheta."""
+        torch = self.torch
+        p = self.problem
+        x0 = torch.as_tensor(x0, dtype=torch.float64, device=self.device).contiguous()
+        ub = (torch.ones(self.Q, dtype=torch.float64, device=self.device) if u0_bar is None
+              else torch.as_tensor(u0_bar, dtype=torch.float64, device=self.device).contiguous())
+        out = {"u0": torch.empty(self.Q, dtype=torch.float64, device=self.device),
+               "grad": torch.empty(self.Q, p.d, dtype=torch.float64, device=self.device),
+               "x0_bar": torch.empty(self.Q, p.d, dtype=torch.float64, device=self.device),
+               "theta_bar": (torch.empty(p.d, dtype=torch.float64, device=self.device)
+                             if with_theta else None)}
+        ws = self._adjoint_workspace()
+        check(fbsde_adjoint(p, self.Q, x0, seed, solve_index0, ub, out["u0"], out["grad"],
+                            out["x0_bar"], out["theta_bar"], ws), "fbsde_adjoint")
+        if check_status:
+            out["status"] = int(fbsde_diagnostics(p, self.Q, ws).status)
+        return out
+
     def solve(self, x0, seed: int, solve_index0: int = 0, trace: bool = False,
               trace_forward: bool = False, check_status: bool = True) -> dict:
         torch = self.torch
@@ -287,6 +330,47 @@ class Solver:
             out["max_newton_iters"] = int(dg.max_newton_iters)
             out["solves_cg_exhausted"] = int(dg.solves_cg_exhausted)
         return out
+
+
+def _make_function():
+    import torch
+
+    class FBSDEValue(torch.autograd.Function):
+        """u(0, x0) of every query as a differentiable function of x0 [Q, d] and (for the
+        kinds with terminal coefficients) theta [d]; backward runs fbsde_adjoint."""
+
+        @staticmethod
+        def forward(ctx, x0, theta, solver, seed, solve_index0):
+            x0 = x0.detach().contiguous()
+            if theta is not None:
+                solver.theta = theta.detach().to(torch.float64).contiguous()
+                solver.problem.theta = solver.theta.data_ptr()
+            out = solver.solve(x0, seed=seed, solve_index0=solve_index0, check_status=False)
+            ctx.solver, ctx.seed, ctx.solve_index0 = solver, seed, solve_index0
+            ctx.has_theta = theta is not None
+            ctx.save_for_backward(x0)
+            return out["u0"]
+
+        @staticmethod
+        def backward(ctx, grad_u0):
+            (x0,) = ctx.saved_tensors
+            adj = ctx.solver.adjoint(x0, ctx.seed, u0_bar=grad_u0.contiguous(),
+                                     solve_index0=ctx.solve_index0,
+                                     with_theta=ctx.has_theta, check_status=False)
+            return adj["x0_bar"], adj["theta_bar"], None, None, None
+
+    return FBSDEValue
+
+
+_FUNCTION = None
+
+
+def fbsde_value(solver: "Solver", x0, seed: int, theta=None, solve_index0: int = 0):
+    """Differentiable u(0, x0) (torch.autograd): gradients flow to x0 and theta."""
+    global _FUNCTION
+    if _FUNCTION is None:
+        _FUNCTION = _make_function()
+    return _FUNCTION.apply(x0, theta, solver, seed, solve_index0)
 
 
 def _main(argv=None) -> None:
