@@ -225,6 +225,41 @@ FBSDE_API int fbsde_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint
 FBSDE_API int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int32_t nj, int32_t d,
                   int32_t precision, void *out, fbsde_stream_t stream);
 
+/*
+ * Plans: a solve, or a batch of heterogeneous solves, captured once into a CUDA graph
+ * and replayed with one launch.  Each CG loop is a conditional while node whose body
+ * (product, reduction, CG step, convergence check) repeats on the device until every
+ * query of that instance has converged, so no empty iterations are launched.  Instances
+ * are spread over parallel graph branches and run concurrently on the GPU.  The
+ * pointers of every instance are bound at creation: refill x0 in place and launch again.
+ */
+typedef struct fbsde_plan fbsde_plan;
+
+typedef struct {
+    fbsde_problem problem;   /* the instance's problem (theta: device pointer)          */
+    int32_t Q;               /* query points of the instance                            */
+    uint32_t solve_index0;   /* Philox solve index of its first query                   */
+    uint64_t seed;           /* Philox key                                              */
+    const double *x0;        /* device [Q][d]                                           */
+    double *u0;              /* device [Q]                                              */
+    double *grad_u0;         /* device [Q][d] or NULL                                   */
+} fbsde_instance;
+
+/* Device workspace bytes of a plan over n instances (their workspaces, 256-aligned). */
+FBSDE_API size_t fbsde_plan_workspace_bytes(int32_t n, const fbsde_instance *inst);
+
+/* Captures the instances into a graph (branches <= 0: min(n, 16) parallel branches) and
+   instantiates it.  The workspace must stay allocated while the plan exists.  Returns
+   FBSDE_ERR_ARG / FBSDE_ERR_WORKSPACE for bad arguments, FBSDE_ERR_CUDA if capture or
+   instantiation fails; *plan is NULL on error. */
+FBSDE_API int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst,
+                                int32_t branches, void *workspace, size_t workspace_bytes);
+/* One graph launch on the stream (asynchronous). */
+FBSDE_API int fbsde_plan_launch(fbsde_plan *plan, fbsde_stream_t stream);
+/* Synchronises the stream and reads the device status of every instance of the plan. */
+FBSDE_API int fbsde_plan_diagnostics(fbsde_plan *plan, fbsde_diag *out, fbsde_stream_t stream);
+FBSDE_API void fbsde_plan_destroy(fbsde_plan *plan);
+
 /* Kernel families of the solve, for the profiler below. */
 typedef enum {
     FBSDE_K_SETUP = 0,      /* per-query set-up                                          */

@@ -2,7 +2,9 @@
 // layout and the launch sequence of Algorithm 1.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include "fbsde_kernels.cuh"
@@ -200,7 +202,7 @@ struct ProfScope {
     cudaStream_t s;
     ProfScope(int family, cudaStream_t st) : s(st)
     {
-        if (!g_prof.on) return;
+        if (!g_prof.on || family < 0) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
         g_prof.launches[family] += 1;
         if (g_prof.used < g_prof.cap) {
@@ -215,19 +217,80 @@ struct ProfScope {
     }
 };
 
+// Where the launches go: eagerly on a stream (with the optional launch profiler), or
+// into a CUDA graph being captured on that stream, with each CG loop as a conditional
+// while node whose body is captured on a second stream.
+struct Rec {
+    cudaStream_t s;
+    bool capture;
+    cudaStream_t body;
+};
+
+#define FBSDE_TRY(fam, call)                                                                 \
+    do {                                                                                     \
+        ProfScope ps_(r.capture ? -1 : (fam), r.s);                                          \
+        if ((e = (call)) != cudaSuccess) return e;                                           \
+    } while (0)
+
+// The CG iterations of one regression (all queries of the launch together).
+template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, const Rec &r)
+{
+    using LR = Launch<Real>;
+    cudaError_t e;
+    const cudaStream_t s = r.s;
+    if (!r.capture) {
+        for (int it = 0; it < p.cg_max_iter; ++it) {
+            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
+        }
+        return cudaSuccess;
+    }
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd)) != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return e;
+    if ((e = LR::cg_check(p, h, 1, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd)) != cudaSuccess) return e;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &np)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return e;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const cudaStream_t b = r.body;
+    if ((e = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return e;
+    cudaError_t eb = LR::matvec(p, L, b);
+    if (eb == cudaSuccess) eb = LR::reduce(p, L, 1, 5, 1, b);
+    if (eb == cudaSuccess) eb = LR::cg_step(p, L, b);
+    if (eb == cudaSuccess) eb = LR::cg_check(p, h, 0, b);
+    cudaGraph_t ended = nullptr;
+    e = cudaStreamEndCapture(b, &ended);
+    return eb != cudaSuccess ? eb : e;
+}
+
 // Algorithm 1: forward sweep, then the backward levels k = N-1..0.  Each level: the CG
 // solve of its regression (moments already reduced), then, for k >= 1, the particle
 // update to level k and the moments of the level k-1 regression.
 template <typename Real>
-cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta, cudaStream_t s)
+cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta, const Rec &r)
 {
     using LR = Launch<Real>;
     cudaError_t e;
-#define FBSDE_TRY(fam, call)                                                                 \
-    do {                                                                                     \
-        ProfScope ps_(fam, s);                                                               \
-        if ((e = (call)) != cudaSuccess) return e;                                           \
-    } while (0)
+    const cudaStream_t s = r.s;
     FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, s));
     FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
     p.level = p.N;
@@ -239,11 +302,7 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
     FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 0, s));
     for (int k = p.N - 1; k >= 0; --k) {
         p.level = k;
-        for (int it = 0; it < p.cg_max_iter; ++it) {
-            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
-            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
-        }
+        if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
         FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
         if (k >= 1) {
             FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
@@ -254,7 +313,6 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
             FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
         }
     }
-#undef FBSDE_TRY
     return cudaSuccess;
 }
 
@@ -265,21 +323,17 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
 template <typename Real>
 cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const double *theta,
                         const double *ubar, double *x0bar, double *thetabar, char *base,
-                        cudaStream_t s)
+                        const Rec &r)
 {
     using LR = Launch<Real>;
     cudaError_t e;
+    const cudaStream_t s = r.s;
     p.tape_w = base + L.off_tape_w;
     p.tape_Y = reinterpret_cast<double *>(base + L.off_tape_Y);
     p.tape_v = reinterpret_cast<double *>(base + L.off_tape_v);
     p.tape_s = reinterpret_cast<double *>(base + L.off_tape_s);
     p.adj_v = reinterpret_cast<double *>(base + L.off_adj_v);
-    if ((e = run<Real>(p, L, x0, theta, s)) != cudaSuccess) return e;
-#define FBSDE_TRY(fam, call)                                                                 \
-    do {                                                                                     \
-        ProfScope ps_(fam, s);                                                               \
-        if ((e = (call)) != cudaSuccess) return e;                                           \
-    } while (0)
+    if ((e = run<Real>(p, L, x0, theta, r)) != cudaSuccess) return e;
     FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_init(p, L, ubar, s));
     int mode_b = 0, mode_c = 0;  // terminal column functions per kind
     switch (p.kind) {
@@ -293,18 +347,14 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
         p.level = k;
         p.w = reinterpret_cast<Real *>(p.tape_w) + (size_t)k * L.Q * L.M;  // weights of level k
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_setup(p, L, s));
-        for (int it = 0; it < p.cg_max_iter; ++it) {
-            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
-            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
-        }
+        if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_post(p, L, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_rows(p, L, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_zlevel(p, L, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_particles(p, L, s));
         const bool terminal = k + 1 == p.N;
-        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_colsum(p, L, terminal ? mode_b : (p.kind == FBSDE_AC_MANUFACTURED ? 1 : 0),
-                                                  terminal ? mode_c : 0, s));
+        const int mb = terminal ? mode_b : (p.kind == FBSDE_AC_MANUFACTURED ? 1 : 0);
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_colsum(p, L, mb, terminal ? mode_c : 0, s));
         FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_finalize(p, L, s));
         if (!terminal) {  // rows Delta_{k+1} -> Delta_{k+2}, regenerating increment k+1
@@ -315,9 +365,10 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
         }
     }
     FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_output(p, L, x0bar, thetabar, s));
-#undef FBSDE_TRY
     return cudaSuccess;
 }
+
+#undef FBSDE_TRY
 
 int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double *theta,
                uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
@@ -335,9 +386,38 @@ int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double
     if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
     const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, trace);
-    const cudaError_t e = P->precision == FBSDE_FP32 ? run<float>(p, L, x0, theta, stream)
-                                                     : run<double>(p, L, x0, theta, stream);
+    const Rec r{stream, false, nullptr};
+    const cudaError_t e = P->precision == FBSDE_FP32 ? run<float>(p, L, x0, theta, r)
+                                                     : run<double>(p, L, x0, theta, r);
     return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Plans.
+// ---------------------------------------------------------------------------
+struct PlanInstance {
+    fbsde_instance in;
+    Layout L;
+    size_t offset;
+};
+
+int plan_layout(int32_t n, const fbsde_instance *inst, std::vector<PlanInstance> &out, size_t &total)
+{
+    if (n < 1 || !inst) return FBSDE_ERR_ARG;
+    out.clear();
+    total = 0;
+    for (int i = 0; i < n; ++i) {
+        PlanInstance pi;
+        pi.in = inst[i];
+        int st = check_problem(&pi.in.problem, pi.in.Q, true);
+        if (st != FBSDE_OK) return st;
+        if ((st = make_layout(&pi.in.problem, pi.in.Q, pi.L)) != FBSDE_OK) return st;
+        if (!pi.in.x0 || !pi.in.u0) return FBSDE_ERR_ARG;
+        pi.offset = total;
+        total = align_up(total + pi.L.total, kAlign);
+        out.push_back(pi);
+    }
+    return FBSDE_OK;
 }
 
 __global__ void k_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n)
@@ -357,6 +437,25 @@ __global__ void k_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out
 }  // namespace fbsde
 
 using namespace fbsde;
+
+struct fbsde_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> streams;   // capture origin, loop bodies, branches
+    std::vector<cudaEvent_t> events;
+    std::vector<PlanInstance> inst;
+    void *workspace = nullptr;
+};
+
+static void plan_free(fbsde_plan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    for (cudaEvent_t e : pl->events) cudaEventDestroy(e);
+    for (cudaStream_t s : pl->streams) cudaStreamDestroy(s);
+    delete pl;
+}
 
 extern "C" {
 
@@ -397,12 +496,12 @@ int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t 
         (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
     const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, nullptr);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Rec r{reinterpret_cast<cudaStream_t>(stream), false, nullptr};
     char *base = static_cast<char *>(workspace);
     const cudaError_t e =
         P->precision == FBSDE_FP32
-            ? run_adjoint<float>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, s)
-            : run_adjoint<double>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, s);
+            ? run_adjoint<float>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, r)
+            : run_adjoint<double>(p, L, x0, P->theta, u0_bar, x0_bar, theta_bar, base, r);
     return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
 }
 
@@ -482,6 +581,116 @@ int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *workspace, 
     *out = d;
     return FBSDE_OK;
 }
+
+size_t fbsde_plan_workspace_bytes(int32_t n, const fbsde_instance *inst)
+{
+    std::vector<PlanInstance> v;
+    size_t total = 0;
+    return plan_layout(n, inst, v, total) == FBSDE_OK ? total : 0;
+}
+
+int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, int32_t branches,
+                      void *workspace, size_t workspace_bytes)
+{
+    if (!plan) return FBSDE_ERR_ARG;
+    *plan = nullptr;
+    std::vector<PlanInstance> v;
+    size_t total = 0;
+    int st = plan_layout(n, inst, v, total);
+    if (st != FBSDE_OK) return st;
+    if (!workspace || workspace_bytes < total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+        return FBSDE_ERR_WORKSPACE;
+    const int B = std::max(1, std::min<int>(n, branches > 0 ? branches : 16));
+    fbsde_plan *pl = new (std::nothrow) fbsde_plan();
+    if (!pl) return FBSDE_ERR_ARG;
+    pl->inst = v;
+    pl->workspace = workspace;
+    auto fail = [&](cudaError_t) {
+        plan_free(pl);
+        return (int)FBSDE_ERR_CUDA;
+    };
+    // streams: 0 = capture origin, 1 = conditional bodies, 2.. = branches
+    for (int i = 0; i < B + 2; ++i) {
+        cudaStream_t sx;
+        if (cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking) != cudaSuccess) return fail(cudaErrorUnknown);
+        pl->streams.push_back(sx);
+    }
+    for (int i = 0; i < B + 1; ++i) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail(cudaErrorUnknown);
+        pl->events.push_back(ev);
+    }
+    // largest-first list scheduling of the instances over the branches
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int i) {
+        const fbsde_problem &P = v[i].in.problem;
+        return (double)v[i].in.Q * P.M * P.d * P.N;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<double> load(B, 0.0);
+    std::vector<std::vector<int>> lists(B);
+    for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[b].push_back(i);
+        load[b] += cost(i);
+    }
+    cudaStream_t origin = pl->streams[0], body = pl->streams[1];
+    if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(cudaErrorUnknown);
+    cudaError_t e = cudaEventRecord(pl->events[0], origin);
+    for (int b = 0; b < B && e == cudaSuccess; ++b)
+        e = cudaStreamWaitEvent(pl->streams[2 + b], pl->events[0], 0);
+    for (int b = 0; b < B && e == cudaSuccess; ++b) {
+        const Rec r{pl->streams[2 + b], true, body};
+        for (int i : lists[b]) {
+            const PlanInstance &pi = v[i];
+            void *ws = static_cast<char *>(workspace) + pi.offset;
+            const Params p = make_params(&pi.in.problem, pi.L, ws, pi.in.seed, pi.in.solve_index0,
+                                         pi.in.u0, pi.in.grad_u0, nullptr);
+            e = pi.in.problem.precision == FBSDE_FP32
+                    ? run<float>(p, pi.L, pi.in.x0, pi.in.problem.theta, r)
+                    : run<double>(p, pi.L, pi.in.x0, pi.in.problem.theta, r);
+            if (e != cudaSuccess) break;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(pl->events[1 + b], pl->streams[2 + b]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, pl->events[1 + b], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(origin, &g);
+    pl->graph = g;
+    if (e != cudaSuccess || ec != cudaSuccess || !g) return fail(e);
+    if (cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) return fail(cudaErrorUnknown);
+    *plan = pl;
+    return FBSDE_OK;
+}
+
+int fbsde_plan_launch(fbsde_plan *plan, fbsde_stream_t stream)
+{
+    if (!plan || !plan->exec) return FBSDE_ERR_ARG;
+    return cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? FBSDE_OK
+               : FBSDE_ERR_CUDA;
+}
+
+int fbsde_plan_diagnostics(fbsde_plan *plan, fbsde_diag *out, fbsde_stream_t stream)
+{
+    if (!plan || !out) return FBSDE_ERR_ARG;
+    fbsde_diag acc{};
+    for (const PlanInstance &pi : plan->inst) {
+        fbsde_diag d{};
+        const int st = fbsde_diagnostics(&pi.in.problem, pi.in.Q,
+                                         static_cast<char *>(plan->workspace) + pi.offset, &d, stream);
+        if (st != FBSDE_OK) return st;
+        if (acc.status == FBSDE_OK) acc.status = d.status;
+        acc.solves_cg_exhausted += d.solves_cg_exhausted;
+        acc.max_newton_iters = std::max(acc.max_newton_iters, d.max_newton_iters);
+    }
+    *out = acc;
+    return FBSDE_OK;
+}
+
+void fbsde_plan_destroy(fbsde_plan *plan) { plan_free(plan); }
 
 int fbsde_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                         fbsde_stream_t stream)

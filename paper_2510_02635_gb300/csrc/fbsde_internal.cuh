@@ -35,7 +35,7 @@ constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-st
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
     double abar, sv, sumz_l, zz_l;  // reverse sweep
-    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all;
+    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, pad2;
 };
 
 struct Layout {
@@ -92,6 +92,8 @@ template <typename Real> struct Launch {
     static cudaError_t moments_finalize(const Params &p, const Layout &L, int warm, cudaStream_t s);
     static cudaError_t cg_step(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t cg_check(const Params &p, cudaGraphConditionalHandle h, int reset,
+                                cudaStream_t s);
     static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
                                void *out, cudaStream_t st);

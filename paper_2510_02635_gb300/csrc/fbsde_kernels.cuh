@@ -1162,6 +1162,26 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     }
 }
 
+// Condition of the CUDA-graph while loop around the CG iterations (default value 1, so
+// the body runs once before the first check): after each pass it stays 1 while some
+// query has not converged and fewer than cg_max_iter passes ran.  reset = 1 (outside
+// the loop) zeroes the pass counter, kept in the first query's state.
+template <typename Real>
+__global__ void k_cg_check(Params p, cudaGraphConditionalHandle h, int reset)
+{
+    if (threadIdx.x != 0) return;
+    int &count = p.st[0].loop_iter;
+    if (reset) {
+        count = 0;
+        return;
+    }
+    count += 1;
+    bool active = false;
+    for (int s = 0; s < p.Q && !active; ++s) active = p.st[s].done == 0;
+    if (count >= p.cg_max_iter) active = false;
+    cudaGraphSetConditional(h, active ? 1u : 0u);
+}
+
 // Trace copy of the forward-sweep end state (X_N - x0 and Y_N) into FP64 arrays.
 template <typename Real> __global__ void k_trace_forward(Params p)
 {

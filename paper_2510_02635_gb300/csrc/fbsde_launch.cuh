@@ -119,6 +119,14 @@ cudaError_t Launch<Real>::cg_post(const Params &p, const Layout &L, cudaStream_t
 }
 
 template <typename Real>
+cudaError_t Launch<Real>::cg_check(const Params &p, cudaGraphConditionalHandle h, int reset,
+                                   cudaStream_t s)
+{
+    dev::k_cg_check<Real><<<1, 32, 0, s>>>(p, h, reset);
+    return cudaGetLastError();
+}
+
+template <typename Real>
 cudaError_t Launch<Real>::trace_forward(const Params &p, const Layout &L, cudaStream_t s)
 {
     const long long n = (long long)p.M * p.d;

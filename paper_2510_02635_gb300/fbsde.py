@@ -50,6 +50,12 @@ class fbsde_trace(C.Structure):
                 ("newton_iters", C.c_void_p), ("x_N", C.c_void_p), ("y_N", C.c_void_p)]
 
 
+class fbsde_instance(C.Structure):
+    _fields_ = [("problem", fbsde_problem), ("Q", C.c_int32), ("solve_index0", C.c_uint32),
+                ("seed", C.c_uint64), ("x0", C.c_void_p), ("u0", C.c_void_p),
+                ("grad_u0", C.c_void_p)]
+
+
 class fbsde_kernel_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("timed", C.c_int64), ("total_ms", C.c_double)]
 
@@ -63,7 +69,9 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_host_staging_bytes", "fbsde_diagnostics", "fbsde_philox4x32_10",
            "fbsde_normals", "fbsde_status_string", "fbsde_abi_version",
            "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
-           "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes"]
+           "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
+           "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
+           "fbsde_plan_diagnostics", "fbsde_plan_destroy"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
 
@@ -111,6 +119,17 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_adjoint_workspace_bytes.restype = SZ
         lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
         lib.fbsde_adjoint.restype = C.c_int
+        IP = C.POINTER(fbsde_instance)
+        lib.fbsde_plan_workspace_bytes.argtypes = [I32, IP]
+        lib.fbsde_plan_workspace_bytes.restype = SZ
+        lib.fbsde_plan_create.argtypes = [C.POINTER(C.c_void_p), I32, IP, I32, V, SZ]
+        lib.fbsde_plan_create.restype = C.c_int
+        lib.fbsde_plan_launch.argtypes = [V, V]
+        lib.fbsde_plan_launch.restype = C.c_int
+        lib.fbsde_plan_diagnostics.argtypes = [V, C.POINTER(fbsde_diag), V]
+        lib.fbsde_plan_diagnostics.restype = C.c_int
+        lib.fbsde_plan_destroy.argtypes = [V]
+        lib.fbsde_plan_destroy.restype = None
         lib.fbsde_abi_version.argtypes = []
         lib.fbsde_abi_version.restype = C.c_int
         _lib = lib
@@ -330,6 +349,65 @@ class Solver:
             out["max_newton_iters"] = int(dg.max_newton_iters)
             out["solves_cg_exhausted"] = int(dg.solves_cg_exhausted)
         return out
+
+
+class Plan:
+    """A batch of (possibly heterogeneous) solves captured once into a CUDA graph.
+
+    instances: list of dicts with keys problem (fbsde_problem), Q, x0 (CUDA tensor
+    [Q, d]), seed, solve_index0 (default 0), grad (bool, default True).  Outputs are
+    allocated here; launch() replays the graph; x0 tensors may be refilled in place."""
+
+    def __init__(self, instances, branches: int = 0, device="cuda"):
+        import torch
+        self.torch = torch
+        lib = load_library()
+        n = len(instances)
+        self.keep = []
+        arr = (fbsde_instance * n)()
+        self.u0, self.grad = [], []
+        for i, spec in enumerate(instances):
+            p = spec["problem"]
+            Q = int(spec["Q"])
+            x0 = spec["x0"]
+            assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous()
+            u = torch.empty(Q, dtype=torch.float64, device=device)
+            g = (torch.empty(Q, p.d, dtype=torch.float64, device=device)
+                 if spec.get("grad", True) else None)
+            self.u0.append(u)
+            self.grad.append(g)
+            self.keep += [x0, u, g, spec.get("theta")]
+            arr[i] = fbsde_instance(p, Q, int(spec.get("solve_index0", 0)), int(spec["seed"]),
+                                    x0.data_ptr(), u.data_ptr(), _ptr(g))
+        self.arr = arr
+        nbytes = int(lib.fbsde_plan_workspace_bytes(n, arr))
+        if nbytes == 0:
+            raise ValueError("invalid plan instances")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        h = C.c_void_p()
+        check(lib.fbsde_plan_create(C.byref(h), n, arr, int(branches), _ptr(self.workspace),
+                                    nbytes), "fbsde_plan_create")
+        self.handle = h
+
+    def launch(self, stream=None) -> None:
+        check(load_library().fbsde_plan_launch(self.handle, _stream(stream)), "fbsde_plan_launch")
+
+    def diagnostics(self, stream=None) -> fbsde_diag:
+        out = fbsde_diag()
+        check(load_library().fbsde_plan_diagnostics(self.handle, C.byref(out), _stream(stream)),
+              "fbsde_plan_diagnostics")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load_library().fbsde_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _make_function():
