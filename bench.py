@@ -172,6 +172,96 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- extras
+def _events_ms(fn, repeats: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(repeats):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / repeats
+
+
+def extra_batched(sample: int = 32) -> dict:
+    """The 512-instance uneven batch in one autotuned FP32 plan (one graph launch per
+    step), and on its first `sample` instances: that batched FP32 plan vs the FP64 form
+    solving the same instances one at a time (one single-instance plan each, launched
+    and completed in turn; capture time excluded on both sides)."""
+    import torch
+
+    from paper_2510_02635_gb300 import autotune, fbsde
+    inst = W.batch_instances()
+    x0s = W.batch_x0(inst)
+    t0 = time.perf_counter()
+    table = autotune.tune(inst)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch = autotune.Batch(inst, x0s, table)
+    create_s = time.perf_counter() - t0
+    ms_full = _events_ms(batch.launch, 2)
+    status = int(batch.plan.diagnostics().status)
+    batch.close()
+    units_full = sum(w.M * w.d * w.N for w in inst)
+    sub, subx = inst[:sample], x0s[:sample]
+    b32 = autotune.Batch(sub, subx, table)
+    ms32 = _events_ms(b32.launch, 2)
+    b32.close()
+    inst64 = W.batch_instances(precision="fp64")[:sample]
+    plans = []
+    for i, (w, x0) in enumerate(zip(inst64, subx)):
+        plans.append(fbsde.Plan([{"problem": autotune.problem_of(w), "Q": 1, "seed": w.seed,
+                                  "x0": torch.tensor(x0, device="cuda"), "solve_index0": i}]))
+
+    def seq64():
+        for pl in plans:
+            pl.launch()
+            torch.cuda.synchronize()
+    ms64 = _events_ms(seq64, 1)
+    for pl in plans:
+        pl.close()
+    units_sub = sum(w.M * w.d * w.N for w in sub)
+    return {"workload": W.BATCH_NAME, "instances": len(inst), "value": units_full / (ms_full * 1e-3),
+            "unit": UNIT, "ms_per_batch": ms_full, "device_status": status,
+            "plan_create_s": create_s, "autotune_s": tune_s,
+            "speedup_sample": {"instances": sample, "fp32_batched_ms": ms32,
+                               "fp64_per_instance_ms": ms64, "ratio": ms64 / ms32,
+                               "fp32_value": units_sub / (ms32 * 1e-3)}}
+
+
+def extra_adjoint() -> dict:
+    """The reverse sweep (d u / d x0, d u / d theta) of the log-quadratic workload vs its
+    primal solve, both eager, CUDA events."""
+    from paper_2510_02635_gb300 import fbsde
+    w = W.C4_HJB_D1000
+    inp = W.inputs(w)
+    solver = fbsde.Solver(w.kind, w.d, w.N, w.M, w.sigma, w.T, Q=w.Q, precision=w.precision,
+                          theta=inp["theta"], cg_tol=w.cg_tol)
+    ms_primal = _events_ms(lambda: solver.solve(inp["x0"], seed=w.seed, check_status=False), 3)
+    ms_adj = _events_ms(lambda: solver.adjoint(inp["x0"], seed=w.seed, with_theta=True,
+                                               check_status=False), 3)
+    return {"workload": w.name, "primal_ms": ms_primal, "adjoint_ms": ms_adj,
+            "adjoint_over_primal": ms_adj / ms_primal,
+            "note": "adjoint = re-run of the solve with its tape + the reverse sweep"}
+
+
+def extra_logistic() -> dict:
+    """The d = 1000, 64-query logistic workload through a plan (device-side CG loops)."""
+    import torch
+
+    from paper_2510_02635_gb300 import autotune, fbsde
+    w = W.C1_LOGISTIC_D1000
+    x0 = torch.tensor(W.inputs(w)["x0"], device="cuda")
+    plan = fbsde.Plan([{"problem": autotune.problem_of(w), "Q": w.Q, "x0": x0, "seed": w.seed}])
+    ms = _events_ms(plan.launch, 5)
+    plan.close()
+    return {"workload": w.name, "value": w.particle_dim_updates / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank: int, world: int) -> None:
     import numpy as np
@@ -281,6 +371,12 @@ def run_gpu(args, rank: int, world: int) -> None:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, levels=2)
         cpu.pop("wall_s")
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        del ws
+        torch.cuda.empty_cache()
+        extras = {"batched": extra_batched(), "adjoint": extra_adjoint(),
+                  "logistic_d1000_plan": extra_logistic()}
 
     if rank == 0:
         line = {
@@ -312,6 +408,7 @@ def run_gpu(args, rank: int, world: int) -> None:
             "u0_sample": float(u[0]),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -325,6 +422,8 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / adjoint / d=1000 measurements")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -105,6 +105,10 @@ typedef struct {
     int32_t cg_max_iter;     /* CG iterations per level; 0 selects 200                 */
     int32_t newton_max_iter; /* Newton iterations per particle; 0 selects 50           */
     double newton_tol;       /* Newton stops when |dY| <= newton_tol max(1,|Y|); 0 selects 1e-13 */
+    int32_t ctas;            /* CTAs of one streaming pass over all Q queries (tiling of the
+                                particle clouds; results depend on it through the order of
+                                the partial sums); 0 selects 608                          */
+    int32_t reserved;        /* must be 0                                               */
 } fbsde_problem;
 
 /* Optional per-level outputs of a solve (all device pointers, each may be NULL).

@@ -45,7 +45,7 @@ int check_problem(const fbsde_problem *P, int32_t Q, bool check_theta)
     if (!(P->T > 0.0) || !std::isfinite(P->T)) return FBSDE_ERR_ARG;
     if (!(P->ridge_rel >= 0.0) || !std::isfinite(P->ridge_rel)) return FBSDE_ERR_ARG;
     if (!(P->cg_tol > 0.0) || P->cg_max_iter < 0 || P->newton_max_iter < 0) return FBSDE_ERR_ARG;
-    if (!(P->newton_tol >= 0.0)) return FBSDE_ERR_ARG;
+    if (!(P->newton_tol >= 0.0) || P->ctas < 0 || P->ctas > (1 << 20)) return FBSDE_ERR_ARG;
     if (check_theta && (P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) &&
         !P->theta)
         return FBSDE_ERR_ARG;
@@ -69,7 +69,8 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     if (!choose_team(nch, L.team_warps, L.vpt, L.teams)) return FBSDE_ERR_ARG;
     L.threads = L.teams * 32 * L.team_warps;
     const long long gmax = std::max<long long>(1, P->M / kMinRowsPerCta);
-    L.G = (int)std::min<long long>(gmax, std::max(1, (kTargetCtas + Q - 1) / Q));
+    const int target = P->ctas > 0 ? P->ctas : kTargetCtas;
+    L.G = (int)std::min<long long>(gmax, std::max(1, (target + Q - 1) / Q));
     // row-segment kernels: one warp per 32 * seg_vpt chunks of a row
     L.seg_vpt = nch >= 128 ? 4 : (nch >= 64 ? 2 : 1);
     L.nseg = (nch + 32 * L.seg_vpt - 1) / (32 * L.seg_vpt);

@@ -28,7 +28,7 @@ constexpr int kPartScal = 4;
 constexpr int kVec64 = 7;
 constexpr int kVecR = 3;
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
-constexpr int kTargetCtas = 608;   // 4 x 152 SMs: CTAs of one streaming pass over all solves
+constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
 constexpr int kMinRowsPerCta = 8;
 constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-stride)
 

@@ -41,7 +41,7 @@ class fbsde_problem(C.Structure):
         ("A", C.c_double), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
         ("c3", C.c_double), ("h", C.c_double), ("ridge_rel", C.c_double),
         ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("newton_max_iter", C.c_int32),
-        ("newton_tol", C.c_double),
+        ("newton_tol", C.c_double), ("ctas", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -157,13 +157,15 @@ def make_problem(kind: str, d: int, N: int, M: int, sigma: float, T: float,
                  precision: str = "fp32", theta=None, A: float = 0.0, c0: float = 0.0,
                  c1: float = 0.0, c2: float = 0.0, c3: float = 0.0, h: float = 2.0,
                  ridge_rel: float = 1e-3, cg_tol: float = 1e-6, cg_max_iter: int = 0,
-                 newton_max_iter: int = 0, newton_tol: float = 0.0) -> fbsde_problem:
+                 newton_max_iter: int = 0, newton_tol: float = 0.0,
+                 ctas: int = 0) -> fbsde_problem:
     """Fill the C problem struct; theta is a device tensor (or host array for the
     host-buffer entry point) whose storage must outlive the call."""
     return fbsde_problem(KINDS[kind], int(d), int(N), PRECISIONS[precision], int(M),
                          float(sigma), float(T), _ptr(theta), float(A), float(c0), float(c1),
                          float(c2), float(c3), float(h), float(ridge_rel), float(cg_tol),
-                         int(cg_max_iter), int(newton_max_iter), float(newton_tol))
+                         int(cg_max_iter), int(newton_max_iter), float(newton_tol), int(ctas),
+                         0)
 
 
 def fbsde_workspace_bytes(problem: fbsde_problem, Q: int) -> int:

@@ -94,3 +94,37 @@ AC_CASE1_D100 = Workload("ac_doublewell_d100_T0.3", "ac_doublewell", d=100,
 
 ALL = {w.name: w for w in (C0_AC_D100, C1_LOGISTIC_D1000, C2_AC_D10000, C4_HJB_D1000,
                            AC_CASE1_D100)}
+
+
+# Batched uneven instances: 512 independent solves in one plan, d log-uniform in
+# [100, 10^4], M in {512, 2048, 8192, 16384}, N in {10, 20, 50}, kinds alternating
+# between the Allen-Cahn problem (sigma = 1, T = 0.5) and the logistic-gradient problem
+# (sigma = d, T = 1), x0 ~ N(0, I/d), seed 3, FP32.
+BATCH_NAME = "batch512_ac_logistic_d100-10000"
+
+
+def batch_instances(n: int = 512, seed: int = 3, precision: str = "fp32",
+                    cg_max_iter: int = 3000) -> list[Workload]:
+    """The n instances of the batched workload (Q = 1 each); instance i uses Philox solve
+    index i.  d, M and N are drawn in instance order from one numpy generator; the query
+    points come from batch_x0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        d = int(round(math.exp(rng.uniform(math.log(100.0), math.log(10000.0)))))
+        M = int(rng.choice([512, 2048, 8192, 16384]))
+        N = int(rng.choice([10, 20, 50]))
+        if i % 2 == 0:
+            kind, sigma, T = "ac_manufactured", 1.0, 0.5
+        else:
+            kind, sigma, T = "logistic_grad", float(d), 1.0
+        out.append(Workload(f"{BATCH_NAME}_{i}", kind, d=d, sigma=sigma, T=T, N=N, M=M, Q=1,
+                            seed=seed, x0_law="normal_1/d", precision=precision,
+                            cg_max_iter=cg_max_iter, extra={"index": i}))
+    return out
+
+
+def batch_x0(instances: list[Workload], seed: int = 3) -> list[np.ndarray]:
+    """x0 of each batched instance ([1, d] each), from a second seeded stream."""
+    rng = np.random.default_rng(seed + 1_000_003)
+    return [rng.standard_normal((1, w.d)) / math.sqrt(w.d) for w in instances]
