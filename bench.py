@@ -204,6 +204,11 @@ def extra_batched(sample: int = 32) -> dict:
     create_s = time.perf_counter() - t0
     ms_full = _events_ms(batch.launch, 2)
     status = int(batch.plan.diagnostics().status)
+    # algorithmic bytes of one batch: per instance 4 B per particle-dim for the forward
+    # write, 12 B per particle-dim per level (update read + write, moments read) and 4 B
+    # per particle-dim per CG product
+    cg = [int(batch.plan.instance_diagnostics(i).cg_iters_total) for i in range(len(inst))]
+    nbytes = sum(4.0 * w.M * w.d * (1 + 3 * w.N + c) for w, c in zip(inst, cg))
     batch.close()
     units_full = sum(w.M * w.d * w.N for w in inst)
     sub, subx = inst[:sample], x0s[:sample]
@@ -226,7 +231,8 @@ def extra_batched(sample: int = 32) -> dict:
     units_sub = sum(w.M * w.d * w.N for w in sub)
     return {"workload": W.BATCH_NAME, "instances": len(inst), "value": units_full / (ms_full * 1e-3),
             "unit": UNIT, "ms_per_batch": ms_full, "device_status": status,
-            "plan_create_s": create_s, "autotune_s": tune_s,
+            "plan_create_s": create_s, "autotune_s": tune_s, "cg_iters_total": sum(cg),
+            "algorithmic_gb": nbytes / 1e9, "effective_gbs": nbytes / (ms_full * 1e-3) / 1e9,
             "speedup_sample": {"instances": sample, "fp32_batched_ms": ms32,
                                "fp64_per_instance_ms": ms64, "ratio": ms64 / ms32,
                                "fp32_value": units_sub / (ms32 * 1e-3)}}

@@ -126,7 +126,7 @@ typedef struct {
     int32_t status;         /* first fbsde_status met by any solve (FBSDE_OK if none)    */
     int32_t solves_cg_exhausted;
     int32_t max_newton_iters;
-    int32_t reserved;
+    int32_t cg_iters_total;  /* CG iterations over all levels and queries of the solve    */
 } fbsde_diag;
 
 /* Bytes of device workspace that fbsde_solve needs for Q query points of problem P.
@@ -252,7 +252,7 @@ typedef struct {
 /* Device workspace bytes of a plan over n instances (their workspaces, 256-aligned). */
 FBSDE_API size_t fbsde_plan_workspace_bytes(int32_t n, const fbsde_instance *inst);
 
-/* Captures the instances into a graph (branches <= 0: min(n, 16) parallel branches) and
+/* Captures the instances into a graph (branches <= 0: min(n, 32) parallel branches) and
    instantiates it.  The workspace must stay allocated while the plan exists.  Returns
    FBSDE_ERR_ARG / FBSDE_ERR_WORKSPACE for bad arguments, FBSDE_ERR_CUDA if capture or
    instantiation fails; *plan is NULL on error. */
@@ -262,6 +262,9 @@ FBSDE_API int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instan
 FBSDE_API int fbsde_plan_launch(fbsde_plan *plan, fbsde_stream_t stream);
 /* Synchronises the stream and reads the device status of every instance of the plan. */
 FBSDE_API int fbsde_plan_diagnostics(fbsde_plan *plan, fbsde_diag *out, fbsde_stream_t stream);
+/* The same for instance `index` (0-based, in creation order) alone. */
+FBSDE_API int fbsde_plan_instance_diagnostics(fbsde_plan *plan, int32_t index, fbsde_diag *out,
+                                              fbsde_stream_t stream);
 FBSDE_API void fbsde_plan_destroy(fbsde_plan *plan);
 
 /* Kernel families of the solve, for the profiler below. */

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_init(Params p, const double
     const double *ax0 = tp.ax(s, 0);
     const double alpha0 = tp.scal(s, 0)[2];
     double a[2] = {0.0, 0.0};  // sum alpha_x, |alpha_x|^2 at level 0
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         a[0] += ax0[i];
         a[1] += ax0[i] * ax0[i];
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_init(Params p, const double
     const double e = exp(-p.T);
     const double us = e * st.phi0 / p.d;
     const double dq = 3.0 * us * us - (2.0 - 0.5 * p.sigma * p.sigma);
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         double zb = 0.0, xb = 0.0;
         if (i < p.d) {
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_setup(Params p)
     Real *pR = ws.vR(s, 0);
     const double abar = st.abar;
     double a[2] = {0.0, 0.0};  // |rhs|^2, S.rhs
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         S[i] = Sk[i];
         const double rhs = ab[i] - abar * Sk[i];
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_post(Params p)
     const double *x = ws.v64(s, 0), *S = ws.v64(s, 3);
     Real *xR = ws.vR(s, 1);
     double a[1] = {0.0};
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         xR[i] = (Real)x[i];
         a[0] += S[i] * x[i];
@@ -395,6 +399,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_finalize(Params p)
     double *ab = tp.av(s, 0), *xb = tp.av(s, 1), *tb = tp.av(s, 2);
     if (L < p.N) {
         const double *axL = tp.ax(s, L);
+        #pragma unroll 4
         for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
             double zb = 0.0;
             if (i < p.d) {
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_zlevel(Params p)
     double a[2] = {0.0, 0.0};
     if (L < p.N) {
         const double *ax = tp.ax(s, L);
+        #pragma unroll 4
         for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
             a[0] += ax[i];
             a[1] += ax[i] * ax[i];

@@ -111,6 +111,7 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
+    L.off_bpart = take(Qs * ((lds + 31) / 32) * sizeof(double));
     L.total = off;
     // reverse sweep: tape of the primal plus three adjoint vectors per query
     L.off_tape_w = take((size_t)P->N * Qs * Ms * L.real_sz);
@@ -171,6 +172,8 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.vec64 = reinterpret_cast<double *>(base + L.off_vec64);
     p.vecR = base + L.off_vecR;
     p.st = reinterpret_cast<SolveState *>(base + L.off_state);
+    p.bpart = reinterpret_cast<double *>(base + L.off_bpart);
+    p.nblk = (L.ld + 31) / 32;
     p.u0 = u0;
     p.grad = grad;
     if (tr) {
@@ -243,7 +246,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
         for (int it = 0; it < p.cg_max_iter; ++it) {
             FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
             FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, 0, 0, s));
         }
         return cudaSuccess;
     }
@@ -276,8 +279,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
         return e;
     cudaError_t eb = LR::matvec(p, L, b);
     if (eb == cudaSuccess) eb = LR::reduce(p, L, 1, 5, 1, b);
-    if (eb == cudaSuccess) eb = LR::cg_step(p, L, b);
-    if (eb == cudaSuccess) eb = LR::cg_check(p, h, 0, b);
+    if (eb == cudaSuccess) eb = LR::cg_step(p, L, h, 1, b);
     cudaGraph_t ended = nullptr;
     e = cudaStreamEndCapture(b, &ended);
     return eb != cudaSuccess ? eb : e;
@@ -577,6 +579,7 @@ int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *workspace, 
         if (d.status == FBSDE_OK && h[q].status != 0) d.status = h[q].status;
         d.solves_cg_exhausted += h[q].cg_exhausted ? 1 : 0;
         d.max_newton_iters = std::max(d.max_newton_iters, h[q].newton_max_all);
+        d.cg_iters_total += h[q].cg_total;
     }
     delete[] h;
     *out = d;
@@ -601,7 +604,7 @@ int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, 
     if (st != FBSDE_OK) return st;
     if (!workspace || workspace_bytes < total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
-    const int B = std::max(1, std::min<int>(n, branches > 0 ? branches : 16));
+    const int B = std::max(1, std::min<int>(n, branches > 0 ? branches : 32));
     fbsde_plan *pl = new (std::nothrow) fbsde_plan();
     if (!pl) return FBSDE_ERR_ARG;
     pl->inst = v;
@@ -624,9 +627,17 @@ int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, 
     // largest-first list scheduling of the instances over the branches
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
+    // work estimate: Q M d N times the passes per level, 2 + the CG iterations, which
+    // grow like the square root of the condition number of the regression: for a cloud
+    // of M points in d dimensions (ratio rho = min(d/M, M/d)) the extreme eigenvalues
+    // are near (1 -+ sqrt(rho))^2, and the ridge bounds the smallest from below.
     auto cost = [&](int i) {
         const fbsde_problem &P = v[i].in.problem;
-        return (double)v[i].in.Q * P.M * P.d * P.N;
+        const double rho = std::min((double)P.d / P.M, (double)P.M / P.d);
+        const double hi = (1.0 + std::sqrt(rho)) * (1.0 + std::sqrt(rho));
+        const double lo = std::max((1.0 - std::sqrt(rho)) * (1.0 - std::sqrt(rho)),
+                                   std::max(P.ridge_rel, 1e-6) * hi);
+        return (double)v[i].in.Q * P.M * P.d * P.N * (2.0 + std::sqrt(hi / lo));
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::vector<double> load(B, 0.0);
@@ -686,9 +697,19 @@ int fbsde_plan_diagnostics(fbsde_plan *plan, fbsde_diag *out, fbsde_stream_t str
         if (acc.status == FBSDE_OK) acc.status = d.status;
         acc.solves_cg_exhausted += d.solves_cg_exhausted;
         acc.max_newton_iters = std::max(acc.max_newton_iters, d.max_newton_iters);
+        acc.cg_iters_total += d.cg_iters_total;
     }
     *out = acc;
     return FBSDE_OK;
+}
+
+int fbsde_plan_instance_diagnostics(fbsde_plan *plan, int32_t index, fbsde_diag *out,
+                                    fbsde_stream_t stream)
+{
+    if (!plan || !out || index < 0 || index >= (int32_t)plan->inst.size()) return FBSDE_ERR_ARG;
+    const PlanInstance &pi = plan->inst[index];
+    return fbsde_diagnostics(&pi.in.problem, pi.in.Q,
+                             static_cast<char *>(plan->workspace) + pi.offset, out, stream);
 }
 
 void fbsde_plan_destroy(fbsde_plan *plan) { plan_free(plan); }

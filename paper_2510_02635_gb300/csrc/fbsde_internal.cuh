@@ -35,7 +35,7 @@ constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-st
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
     double abar, sv, sumz_l, zz_l;  // reverse sweep
-    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, pad2;
+    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive, pad3;
 };
 
 struct Layout {
@@ -46,7 +46,7 @@ struct Layout {
     int64_t M;
     size_t real_sz;
     size_t off_delta, off_Y, off_w, off_coef, off_segp, off_part, off_spart, off_vec64, off_vecR,
-        off_state;
+        off_state, off_bpart;
     size_t total;
 };
 
@@ -54,7 +54,7 @@ struct Layout {
 struct Params {
     // problem
     int kind, d, ld, N, G, team_warps, level, uniform, cg_max_iter, newton_max_iter, has_r,
-        newton_level, Q, nseg, GP, GS, mv_rows, mv_stages, walk;
+        newton_level, Q, nseg, GP, GS, mv_rows, mv_stages, walk, nblk;
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
     uint32_t key0, key1, solve0;
@@ -69,6 +69,7 @@ struct Params {
     double *vec64;
     void *vecR;
     SolveState *st;
+    double *bpart;  // [Q][nblk] per-block shares of p.q of the CG product
     // tape of the primal for the reverse sweep (null when not recording)
     void *tape_w;
     double *tape_Y, *tape_v, *tape_s, *adj_v;
@@ -90,7 +91,8 @@ template <typename Real> struct Launch {
                               cudaStream_t s);
     static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t moments_finalize(const Params &p, const Layout &L, int warm, cudaStream_t s);
-    static cudaError_t cg_step(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t cg_step(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
+                               int use_h, cudaStream_t s);
     static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t cg_check(const Params &p, cudaGraphConditionalHandle h, int reset,
                                 cudaStream_t s);

@@ -372,88 +372,6 @@ template <typename T, int NV> __device__ __forceinline__ void warp_sum(T (&v)[NV
 }
 
 // ---------------------------------------------------------------------------
-// mbarrier + bulk-copy (TMA) helpers.  Every wait is bounded: after kWaitNs of
-// %globaltimer without completion it returns false and the caller records
-// FBSDE_ERR_TIMEOUT instead of spinning forever.
-// ---------------------------------------------------------------------------
-constexpr unsigned long long kWaitNs = 5ull * 1000 * 1000 * 1000;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
-{
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        "  .reg .pred q;\n"
-        "  mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
-        "  selp.u32 %0, 1, 0, q;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits for the completion of the barrier phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitNs) return false;
-    }
-}
-// Bounded wait whose failure is sticky: after the first timeout of this thread, later
-// waits only poll once, so a broken pipeline costs one kWaitNs per thread, not one per
-// stage.
-__device__ __forceinline__ void mbar_wait_or_flag(uint64_t *bar, uint32_t parity, bool &timed_out)
-{
-    if (timed_out) {
-        (void)mbar_try_wait(bar, parity);
-        return;
-    }
-    if (!mbar_wait(bar, parity)) timed_out = true;
-}
-
-// Bulk copy global -> shared memory; completion is signalled on bar as transaction bytes.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// ---------------------------------------------------------------------------
 // Row-segment kernels.  Work item = (query s, particle j, segment); one warp per item,
 // lane l holding chunks c0 + l + 32 v (v < VPT) of the segment.  Each item writes its
 // warp sums to segp; the per-particle kernel adds the segments in order.  No barriers,
@@ -757,178 +675,59 @@ __global__ void __launch_bounds__(256) k_moments(Params p)
     }
 }
 
-// Sum of the G per-CTA partials, in CTA order, in FP64: vectors 0..nvec-1 of part into
-// v64 slots dst0..dst0+nvec-1.  Grid (ceil(ld/256), Q).  skip_done: CG products of
-// converged queries are skipped.
+// Sum of the G per-CTA partials in FP64 in a fixed order.  Block = 32 elements x 8
+// groups: group gg adds partials g = gg, gg + 8, ... in order, then the 8 group sums are
+// added in group order.  cg_mode = 0: vectors 0..nvec-1 into v64 slots dst0..; cg_mode = 1
+// (CG product, converged queries skipped): q = sum / W - S (S.p) + lambda p into slot 5 and
+// the block's share of p.q into bpart.  Grid (ceil(ld / 32), Q).
 template <typename Real>
-__global__ void __launch_bounds__(256) k_reduce_partials(Params p, int nvec, int dst0, int skip_done)
+__global__ void __launch_bounds__(256) k_reduce_partials(Params p, int nvec, int dst0, int cg_mode)
 {
+    __shared__ double sm[8][33];
     const int s = blockIdx.y;
-    if (skip_done && p.st[s].done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.ld) return;
+    if (cg_mode && p.st[s].done) return;
+    const int ii = threadIdx.x & 31, gg = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + ii;
     const WS<Real> ws(p);
+    const size_t stride = (size_t)kPartVecs * p.ld;
     for (int v = 0; v < nvec; ++v) {
-        const Real *src = ws.part(s, 0, v) + i;
-        const size_t stride = (size_t)kPartVecs * p.ld;
         double acc = 0.0;
-        int g = 0;
-        for (; g + 8 <= p.G; g += 8) {
-            Real t[8];
+        if (i < p.ld) {
+            const Real *src = ws.part(s, 0, v) + i;
+            int g = gg;
+            for (; g + 24 < p.G; g += 32) {
+                Real t[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = src[(size_t)(g + u) * stride];
+                for (int u = 0; u < 4; ++u) t[u] = src[(size_t)(g + 8 * u) * stride];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += (double)t[u];
+                for (int u = 0; u < 4; ++u) acc += (double)t[u];
+            }
+            for (; g < p.G; g += 8) acc += (double)src[(size_t)g * stride];
         }
-        for (; g < p.G; ++g) acc += (double)src[(size_t)g * stride];
-        ws.v64(s, dst0 + v)[i] = acc;
+        sm[gg][ii] = acc;
+        __syncthreads();
+        if (gg == 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) tot += sm[k][ii];
+            if (!cg_mode) {
+                if (i < p.ld) ws.v64(s, dst0 + v)[i] = tot;
+            } else {
+                const SolveState &st = p.st[s];
+                double pq = 0.0;
+                if (i < p.ld) {
+                    const double pi = ws.v64(s, 2)[i];
+                    const double qi = tot * st.invW - ws.v64(s, 3)[i] * st.sp + st.lambda * pi;
+                    ws.v64(s, 5)[i] = qi;
+                    pq = pi * qi;
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, o);
+                if (ii == 0) p.bpart[(size_t)s * p.nblk + blockIdx.x] = pq;
+            }
+        }
+        __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------------------
-// Matrix-free product of the regression (Sec. 2.4, Steps 1 and 2) on the centred
-// operator: partial_g = sum_{j in CTA g} w_j (D_j . v) D_j with v = vR(s, 0).
-// Warp 0 is the producer: one lane streams the CTA's rows, mv_rows consecutive rows
-// (one contiguous block) per stage, into a ring of mv_stages shared-memory stages
-// with cp.async.bulk, completion counted on the stage's "full" mbarrier.  The other
-// warps form nteams consumer teams of team_warps warps; a team owns one row at a time:
-// dot product from shared memory, team sum (warp butterfly + one named barrier),
-// then the weighted row sum into register accumulators.  Each consumer warp arrives
-// on the stage's "empty" mbarrier when done, which lets the producer refill it.
-// ---------------------------------------------------------------------------
-template <typename Real, int VPT, bool WIDE>
-__global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matvec(Params p)
-{
-    constexpr int E = Chunk<Real>::E;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int g = blockIdx.x, s = blockIdx.y;
-    if (p.st[s].done) return;
-    const WS<Real> ws(p);
-    const int nch = p.ld / E;
-    const int S = p.mv_stages, R = p.mv_rows;
-    const int tw = p.team_warps;
-    const int nteams = (blockDim.x / 32 - 1) / tw;
-    const size_t row_elems = (size_t)p.ld;
-    const uint32_t row_bytes = (uint32_t)(row_elems * sizeof(Real));
-    Real *ring = reinterpret_cast<Real *>(smem_raw);                     // [S][R][ld]
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + (size_t)S * R * row_elems);
-    uint64_t *empty = full + S;
-    Real *slots = reinterpret_cast<Real *>(empty + S);                   // [nteams][2][32]
-    long long r0, r1;
-    row_range(p.M, p.G, g, r0, r1);
-    const long long nst = (r1 - r0 + R - 1) / R;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < S; ++st) {
-            mbar_init(&full[st], 1);
-            mbar_init(&empty[st], nteams * tw);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    bool timed_out = false;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            for (long long i = 0; i < nst; ++i) {
-                const int st = (int)(i % S);
-                const uint32_t par = (uint32_t)((i / S) & 1);
-                if (i >= S) mbar_wait_or_flag(&empty[st], par ^ 1u, timed_out);
-                const long long row0 = r0 + i * R;
-                const uint32_t rows = (uint32_t)min((long long)R, r1 - row0);
-                mbar_arrive_expect_tx(&full[st], rows * row_bytes);
-                bulk_g2s(ring + (size_t)st * R * row_elems, ws.row(s, row0), rows * row_bytes,
-                         &full[st]);
-            }
-            // drain: the last copy into every stage has landed before the CTA can exit
-            for (long long i = max(0ll, nst - S); i < nst; ++i)
-                mbar_wait_or_flag(&full[i % S], (uint32_t)((i / S) & 1), timed_out);
-        }
-    } else {
-        const int ct = threadIdx.x - 32;
-        const int tthreads = 32 * tw;
-        const int team = ct / tthreads, tl = ct - team * tthreads, wt = tl >> 5;
-        const Real *pv = ws.vR(s, 0);
-        const Real *wv = ws.w(s);
-        Chunk<Real> acc[VPT], pc[VPT];
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            zero(acc[v]);
-            const int c = tl + tthreads * v;
-            if (c < nch) pc[v] = ldg_chunk(pv + c * E);
-            else zero(pc[v]);
-        }
-        int phase = 0;
-        for (long long i = 0; i < nst; ++i) {
-            const int st = (int)(i % S);
-            mbar_wait_or_flag(&full[st], (uint32_t)((i / S) & 1), timed_out);
-            const long long row0 = r0 + i * R;
-            const int rows = (int)min((long long)R, r1 - row0);
-            const Real *buf = ring + (size_t)st * R * row_elems;
-            for (int rr = team; rr < rows; rr += nteams) {
-                const Real *row = buf + (size_t)rr * row_elems;
-                Real t = Real(0);
-#pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int c = tl + tthreads * v;
-                    if (c < nch) {
-                        const Chunk<Real> dl = ld_chunk(row + c * E);
-#pragma unroll
-                        for (int e = 0; e < E; ++e) t += dl.v[e] * pc[v].v[e];
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (tw > 1) {
-                    Real *sl = slots + (size_t)(team * 2 + phase) * 32;
-                    if (lane == 0) sl[wt] = t;
-                    bar_named(1 + team, tthreads);
-                    t = Real(0);
-                    for (int w2 = 0; w2 < tw; ++w2) t += sl[w2];
-                    phase ^= 1;
-                }
-                const Real coef = wv[row0 + rr] * t;
-#pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int c = tl + tthreads * v;
-                    if (c < nch) {
-                        const Chunk<Real> dl = ld_chunk(row + c * E);
-#pragma unroll
-                        for (int e = 0; e < E; ++e) acc[v].v[e] += coef * dl.v[e];
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
-        }
-        // team accumulators -> CTA partial (teams summed in team order via the ring)
-        Real *dst = ws.part(s, g, 0);
-        if (nteams == 1) {
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int c = tl + tthreads * v;
-                if (c < nch) st_chunk(dst + c * E, acc[v]);
-            }
-        } else {
-            bar_named(15, 32 * nteams * tw);   // every consumer is past its last ring read
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int c = tl + tthreads * v;
-                if (c < nch) st_chunk(ring + (size_t)team * row_elems + c * E, acc[v]);
-            }
-            bar_named(15, 32 * nteams * tw);
-            for (int c = ct; c < nch; c += 32 * nteams * tw) {
-                Chunk<Real> sum = ld_chunk(ring + c * E);
-                for (int t2 = 1; t2 < nteams; ++t2) {
-                    const Chunk<Real> o = ld_chunk(ring + (size_t)t2 * row_elems + c * E);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) sum.v[e] += o.v[e];
-                }
-                st_chunk(dst + c * E, sum);
-            }
-        }
-    }
-    if (timed_out) atomicCAS(&p.st[s].status, 0, (int)FBSDE_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,6 +742,7 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
     double *x = ws.v64(s, 0), *x0v = ws.v64(s, 6);
     Real *pR = ws.vR(s, 0), *xR = ws.vR(s, 1), *x0R = ws.vR(s, 2);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};  // sum cos, sum x, sum x^2, theta-weighted sum
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = i < p.d ? x0[(size_t)s * p.d + i] : 0.0;
         const double th = (theta && i < p.d) ? theta[i] : 0.0;
@@ -1006,6 +806,7 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
            *B = ws.v64(s, 4), *Gx = ws.v64(s, 5);
     Real *pR = ws.vR(s, 0);
     double a1[2] = {0.0, 0.0};  // |S|^2, S.x
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         S[i] *= invW;
         B[i] *= invW;
@@ -1018,6 +819,7 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     const double lambda = p.ridge_rel * (Rr * invW - a1[0]) / p.d;
     const double sx = a1[1];
     double a2[3] = {0.0, 0.0, 0.0};  // |rhs|^2, |r|^2, S.r
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double rhs = B[i] - cp * S[i];
         const double ri = rhs - (Gx[i] - S[i] * sx) - lambda * x[i];
@@ -1031,6 +833,7 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     }
     if (p.tape_v) {
         double *tS = p.tape_v + (((size_t)s * p.N + (p.level - 1)) * 2 + 0) * p.ld;
+        #pragma unroll 4
         for (int i = threadIdx.x; i < p.ld; i += blockDim.x) tS[i] = S[i];
     }
     block_sum(a2, sm);
@@ -1053,62 +856,82 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     }
 }
 
-// One CG step after q_sum = sum_g partial (FP64, slot 5):
-//   q = q_sum/W - S (S.p) + lambda p,  a = rr/(p.q),  x += a p,  r -= a q,
-//   p = r + (rr'/rr) p.
+// One CG step after the product reduction (q in slot 5, p.q by reduction block):
+//   a = rr/(p.q),  x += a p,  r -= a q,  p = r + (rr'/rr) p.
+// In a CUDA graph (use_h = 1) the last CTA to finish sets the while-loop condition: 1
+// while some query has not converged and fewer than cg_max_iter passes ran.
 template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_cg_step(Params p)
+__global__ void __launch_bounds__(kFinThreads) k_cg_step(Params p, cudaGraphConditionalHandle h,
+                                                         int use_h)
 {
     __shared__ double sm[32 * 4];
+    __shared__ double pq_sh;
     const int s = blockIdx.x;
     SolveState &st = p.st[s];
-    if (st.done) return;
-    const WS<Real> ws(p);
-    double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
-           *q = ws.v64(s, 5);
-    Real *pR = ws.vR(s, 0);
-    const double invW = st.invW, lambda = st.lambda, sp = st.sp, rr = st.rr;
-    double a[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        const double qi = q[i] * invW - S[i] * sp + lambda * pp[i];
-        q[i] = qi;
-        a[0] += pp[i] * qi;
-    }
-    block_sum(a, sm);
-    if (!(a[0] > 0.0) || !isfinite(a[0])) {  // breakdown: keep the current iterate
+    if (!st.done) {
+        const WS<Real> ws(p);
+        double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
+               *q = ws.v64(s, 5);
+        Real *pR = ws.vR(s, 0);
+        const double rr = st.rr;
         if (threadIdx.x == 0) {
-            st.done = 1;
-            if (!(rr <= p.cg_tol2 * st.rhs2) && st.status == 0) st.status = FBSDE_ERR_CG;
+            double a = 0.0;
+            for (int b = 0; b < p.nblk; ++b) a += p.bpart[(size_t)s * p.nblk + b];
+            pq_sh = a;
         }
-        return;
+        __syncthreads();
+        const double pq = pq_sh;
+        if (!(pq > 0.0) || !isfinite(pq)) {  // breakdown: keep the current iterate
+            if (threadIdx.x == 0) {
+                st.done = 1;
+                if (!(rr <= p.cg_tol2 * st.rhs2) && st.status == 0) st.status = FBSDE_ERR_CG;
+            }
+        } else {
+            const double step = rr / pq;
+            double b1[1] = {0.0};
+            #pragma unroll 4
+            for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+                x[i] += step * pp[i];
+                r[i] -= step * q[i];
+                b1[0] += r[i] * r[i];
+            }
+            block_sum(b1, sm);
+            const double rr_new = b1[0], beta = rr_new / rr;
+            double c1[1] = {0.0};
+            #pragma unroll 4
+            for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+                const double pi = r[i] + beta * pp[i];
+                pp[i] = pi;
+                pR[i] = (Real)pi;
+                c1[0] += S[i] * pi;
+            }
+            block_sum(c1, sm);
+            if (threadIdx.x == 0) {
+                st.rr = rr_new;
+                st.sp = c1[0];
+                st.iters += 1;
+                st.cg_total += 1;
+                const bool conv = rr_new <= p.cg_tol2 * st.rhs2;
+                if (conv) st.done = 1;
+                else if (st.iters >= p.cg_max_iter) {
+                    st.done = 1;
+                    st.cg_exhausted += 1;
+                    if (st.status == 0) st.status = FBSDE_ERR_CG;
+                }
+            }
+        }
     }
-    const double step = rr / a[0];
-    double b[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        x[i] += step * pp[i];
-        r[i] -= step * q[i];
-        b[0] += r[i] * r[i];
-    }
-    block_sum(b, sm);
-    const double rr_new = b[0], beta = rr_new / rr;
-    double c[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        const double pi = r[i] + beta * pp[i];
-        pp[i] = pi;
-        pR[i] = (Real)pi;
-        c[0] += S[i] * pi;
-    }
-    block_sum(c, sm);
-    if (threadIdx.x == 0) {
-        st.rr = rr_new;
-        st.sp = c[0];
-        st.iters += 1;
-        const bool conv = rr_new <= p.cg_tol2 * st.rhs2;
-        if (conv) st.done = 1;
-        else if (st.iters >= p.cg_max_iter) {
-            st.done = 1;
-            st.cg_exhausted += 1;
-            if (st.status == 0) st.status = FBSDE_ERR_CG;
+    if (use_h && threadIdx.x == 0) {
+        __threadfence();
+        const int arrived = atomicAdd(&p.st[0].arrive, 1);
+        if (arrived == p.Q - 1) {
+            p.st[0].arrive = 0;
+            const int count = ++p.st[0].loop_iter;
+            bool active = false;
+            for (int q2 = 0; q2 < p.Q && !active; ++q2)
+                active = *reinterpret_cast<volatile int *>(&p.st[q2].done) == 0;
+            if (count >= p.cg_max_iter) active = false;
+            cudaGraphSetConditional(h, active ? 1u : 0u);
         }
     }
 }
@@ -1125,6 +948,7 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     const double *x = ws.v64(s, 0), *S = ws.v64(s, 3);
     Real *xR = ws.vR(s, 1);
     double a[3] = {0.0, 0.0, 0.0};
+    #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = x[i];
         xR[i] = (Real)xi;
@@ -1173,6 +997,7 @@ __global__ void k_cg_check(Params p, cudaGraphConditionalHandle h, int reset)
     int &count = p.st[0].loop_iter;
     if (reset) {
         count = 0;
+        p.st[0].arrive = 0;
         return;
     }
     count += 1;

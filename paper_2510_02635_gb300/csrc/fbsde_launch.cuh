@@ -2,6 +2,7 @@
 #pragma once
 #include "fbsde_adjoint.cuh"
 #include "fbsde_kernels.cuh"
+#include "fbsde_matvec.cuh"
 
 namespace fbsde {
 
@@ -67,8 +68,8 @@ template <typename Real>
 cudaError_t Launch<Real>::reduce(const Params &p, const Layout &L, int nvec, int dst0,
                                  int skip_done, cudaStream_t s)
 {
-    dev::k_reduce_partials<Real><<<dim3((L.ld + 255) / 256, L.Q), 256, 0, s>>>(p, nvec, dst0,
-                                                                              skip_done);
+    dev::k_reduce_partials<Real><<<dim3((L.ld + 31) / 32, L.Q), 256, 0, s>>>(p, nvec, dst0,
+                                                                             skip_done);
     return cudaGetLastError();
 }
 
@@ -105,9 +106,10 @@ cudaError_t Launch<Real>::moments_finalize(const Params &p, const Layout &L, int
 }
 
 template <typename Real>
-cudaError_t Launch<Real>::cg_step(const Params &p, const Layout &L, cudaStream_t s)
+cudaError_t Launch<Real>::cg_step(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
+                                  int use_h, cudaStream_t s)
 {
-    dev::k_cg_step<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    dev::k_cg_step<Real><<<L.Q, kFinThreads, 0, s>>>(p, h, use_h);
     return cudaGetLastError();
 }
 

@@ -62,7 +62,7 @@ class fbsde_kernel_stats(C.Structure):
 
 class fbsde_diag(C.Structure):
     _fields_ = [("status", C.c_int32), ("solves_cg_exhausted", C.c_int32),
-                ("max_newton_iters", C.c_int32), ("reserved", C.c_int32)]
+                ("max_newton_iters", C.c_int32), ("cg_iters_total", C.c_int32)]
 
 
 EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
@@ -71,7 +71,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
            "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
-           "fbsde_plan_diagnostics", "fbsde_plan_destroy"]
+           "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
 
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_plan_launch.restype = C.c_int
         lib.fbsde_plan_diagnostics.argtypes = [V, C.POINTER(fbsde_diag), V]
         lib.fbsde_plan_diagnostics.restype = C.c_int
+        lib.fbsde_plan_instance_diagnostics.argtypes = [V, I32, C.POINTER(fbsde_diag), V]
+        lib.fbsde_plan_instance_diagnostics.restype = C.c_int
         lib.fbsde_plan_destroy.argtypes = [V]
         lib.fbsde_plan_destroy.restype = None
         lib.fbsde_abi_version.argtypes = []
@@ -398,6 +400,13 @@ class Plan:
         out = fbsde_diag()
         check(load_library().fbsde_plan_diagnostics(self.handle, C.byref(out), _stream(stream)),
               "fbsde_plan_diagnostics")
+        return out
+
+    def instance_diagnostics(self, index: int, stream=None) -> fbsde_diag:
+        out = fbsde_diag()
+        check(load_library().fbsde_plan_instance_diagnostics(self.handle, int(index),
+                                                             C.byref(out), _stream(stream)),
+              "fbsde_plan_instance_diagnostics")
         return out
 
     def close(self) -> None:
