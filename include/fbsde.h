@@ -294,8 +294,14 @@ typedef struct {
    host threads).  After fbsde_profile_start(n), every launch is counted and the first
    n launches are bracketed by CUDA events recorded on the launching stream.
    fbsde_profile_stop() waits for the recorded events, fills out[FBSDE_NUM_KERNELS]
-   and switches the profiler off. */
+   and switches the profiler off.  fbsde_profile_select(mask) restricts the timing to
+   the families whose bit (1u << family) is set (all of them by default, and again after
+   each fbsde_profile_stop); launches of the other families are still counted.  Each
+   timed launch adds two event records to its stream, so timing only the family of
+   interest keeps the profiler's own cost out of the rest of the step.  ERR_ARG for a
+   mask with no valid family bit. */
 FBSDE_API int fbsde_profile_start(int32_t max_timed_launches);
+FBSDE_API int fbsde_profile_select(uint32_t family_mask);
 FBSDE_API int fbsde_profile_stop(fbsde_kernel_stats *out);
 FBSDE_API const char *fbsde_kernel_name(int family);
 

@@ -91,6 +91,10 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
                     (size_t)L.teams * 2 * 32 * L.real_sz;
         if (L.mv_smem > 227 * 1024) return FBSDE_ERR_ARG;
     }
+    // partial reduction: tiles of kRedTile elements, red_groups warps per tile, each adding
+    // about four of the G partials
+    L.nblk = (L.ld + kRedTile - 1) / kRedTile;
+    L.red_groups = std::min(16, std::max(4, (L.G + 3) / 4));
     // moments: column tiles of 256 * mom_vm chunks
     L.mom_vm = nch > 256 ? 2 : 1;
     L.mom_tiles = (nch + 256 * L.mom_vm - 1) / (256 * L.mom_vm);
@@ -111,7 +115,7 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
-    L.off_bpart = take(Qs * ((lds + 31) / 32) * sizeof(double));
+    L.off_bpart = take(Qs * (size_t)L.nblk * kBpart * sizeof(double));
     L.total = off;
     // reverse sweep: tape of the primal plus three adjoint vectors per query
     L.off_tape_w = take((size_t)P->N * Qs * Ms * L.real_sz);
@@ -173,7 +177,7 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.vecR = base + L.off_vecR;
     p.st = reinterpret_cast<SolveState *>(base + L.off_state);
     p.bpart = reinterpret_cast<double *>(base + L.off_bpart);
-    p.nblk = (L.ld + 31) / 32;
+    p.nblk = L.nblk;
     p.u0 = u0;
     p.grad = grad;
     if (tr) {
@@ -195,6 +199,7 @@ struct Profiler {
     std::mutex mu;
     bool on = false;
     int cap = 0, used = 0;
+    uint32_t mask = (1u << FBSDE_NUM_KERNELS) - 1;
     std::vector<cudaEvent_t> ev;
     std::vector<int> fam;
     int64_t launches[FBSDE_NUM_KERNELS] = {};
@@ -209,7 +214,7 @@ struct ProfScope {
         if (!g_prof.on || family < 0) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
         g_prof.launches[family] += 1;
-        if (g_prof.used < g_prof.cap) {
+        if (((g_prof.mask >> family) & 1u) && g_prof.used < g_prof.cap) {
             slot = g_prof.used++;
             g_prof.fam[slot] = family;
             cudaEventRecord(g_prof.ev[2 * slot], s);
@@ -246,7 +251,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
         for (int it = 0; it < p.cg_max_iter; ++it) {
             FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
             FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_step(p, L, 0, 0, s));
+            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_update(p, L, 0, 0, s));
         }
         return cudaSuccess;
     }
@@ -260,7 +265,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
     cudaGraphConditionalHandle h;
     if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
-    if ((e = LR::cg_check(p, h, 1, s)) != cudaSuccess) return e;
+    if ((e = LR::cg_reset(p, s)) != cudaSuccess) return e;
     if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd)) != cudaSuccess) return e;
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
@@ -279,7 +284,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
         return e;
     cudaError_t eb = LR::matvec(p, L, b);
     if (eb == cudaSuccess) eb = LR::reduce(p, L, 1, 5, 1, b);
-    if (eb == cudaSuccess) eb = LR::cg_step(p, L, h, 1, b);
+    if (eb == cudaSuccess) eb = LR::cg_update(p, L, h, 1, b);
     cudaGraph_t ended = nullptr;
     e = cudaStreamEndCapture(b, &ended);
     return eb != cudaSuccess ? eb : e;
@@ -753,10 +758,20 @@ int fbsde_profile_start(int32_t max_timed_launches)
     return FBSDE_OK;
 }
 
+int fbsde_profile_select(uint32_t family_mask)
+{
+    const uint32_t all = (1u << FBSDE_NUM_KERNELS) - 1;
+    if (!(family_mask & all)) return FBSDE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.mask = family_mask & all;
+    return FBSDE_OK;
+}
+
 int fbsde_profile_stop(fbsde_kernel_stats *out)
 {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     g_prof.on = false;
+    g_prof.mask = (1u << FBSDE_NUM_KERNELS) - 1;
     int st = FBSDE_OK;
     fbsde_kernel_stats acc[FBSDE_NUM_KERNELS] = {};
     for (int f = 0; f < FBSDE_NUM_KERNELS; ++f) acc[f].launches = g_prof.launches[f];

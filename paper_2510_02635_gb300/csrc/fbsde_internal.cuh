@@ -25,7 +25,9 @@ namespace fbsde {
 
 constexpr int kPartVecs = 3;
 constexpr int kPartScal = 4;
-constexpr int kVec64 = 7;
+constexpr int kVec64 = 8;
+constexpr int kRedTile = 128;  // elements per block of the partial reduction and CG update
+constexpr int kBpart = 4;      // per-block shares: w . r, S . r, r . r, spare
 constexpr int kVecR = 3;
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
@@ -35,13 +37,16 @@ constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-st
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
     double abar, sv, sumz_l, zz_l;  // reverse sweep
-    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive, pad3;
+    double rr_prev, cg_alpha;       // previous r . r and step of the CG recurrence
+    double cg_beta, cg_step;        // scalars of the current CG pass
+    int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive,
+        arrive_q, cg_ok, pad4;
 };
 
 struct Layout {
     int Q, d, ld, N, G, precision, team_warps, vpt, teams, threads;
     size_t off_tape_w, off_tape_Y, off_tape_v, off_tape_s, off_adj_v, total_adjoint;
-    int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks, mv_rows, mv_stages;
+    int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks, mv_rows, mv_stages, red_groups, nblk;
     size_t mv_smem;
     int64_t M;
     size_t real_sz;
@@ -69,7 +74,7 @@ struct Params {
     double *vec64;
     void *vecR;
     SolveState *st;
-    double *bpart;  // [Q][nblk] per-block shares of p.q of the CG product
+    double *bpart;  // [Q][nblk][kBpart] per-block shares of the CG dot products
     // tape of the primal for the reverse sweep (null when not recording)
     void *tape_w;
     double *tape_Y, *tape_v, *tape_s, *adj_v;
@@ -91,11 +96,10 @@ template <typename Real> struct Launch {
                               cudaStream_t s);
     static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t moments_finalize(const Params &p, const Layout &L, int warm, cudaStream_t s);
-    static cudaError_t cg_step(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
+    static cudaError_t cg_update(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
                                int use_h, cudaStream_t s);
     static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
-    static cudaError_t cg_check(const Params &p, cudaGraphConditionalHandle h, int reset,
-                                cudaStream_t s);
+    static cudaError_t cg_reset(const Params &p, cudaStream_t s);
     static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
                                void *out, cudaStream_t st);

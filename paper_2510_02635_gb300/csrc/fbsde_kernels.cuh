@@ -11,8 +11,10 @@
 //   k_moments              streaming weighted column sums of the particle rows;
 //   k_matvec               the matrix-free product of the regression operator (a team
 //                          of warps per row: dot product, then the weighted row sum);
-//   k_reduce_partials      fixed-order FP64 sum of the per-CTA partial vectors;
-//   k_moments_finalize, k_cg_step, k_cg_post, k_setup
+//   k_reduce_partials      fixed-order compensated sum of the per-CTA partial vectors,
+//                          and in the CG the operator's FP64 epilogue (tiles of 128);
+//   k_cg_update            one CG pass of the d-vectors, tiles of 128 elements per block;
+//   k_moments_finalize, k_cg_post, k_setup
 //                          one CTA per query: FP64 d-vector algebra of the regression.
 #pragma once
 #include <math.h>
@@ -340,12 +342,14 @@ template <typename Real> struct WS {
     {
         return p.spart + ((size_t)s * p.GS + b) * kPartScal;
     }
-    // FP64 vectors: 0 x (= alpha_x), 1 r, 2 p, 3 S, 4 b / rhs, 5 q or G, 6 x0
+    // FP64 vectors: 0 x (= alpha_x), 1 r, 2 p, 3 S, 4 b / rhs, 5 w = A r or G, 6 x0,
+    // 7 s = A p
     __device__ __forceinline__ double *v64(int s, int which) const
     {
         return p.vec64 + ((size_t)s * kVec64 + which) * p.ld;
     }
-    // stream-precision vectors: 0 p, 1 x, 2 x0; theta after all solves
+    // stream-precision vectors: 0 operand of the product (r), 1 x, 2 x0; theta after all
+    // solves
     __device__ __forceinline__ Real *vR(int s, int which) const
     {
         return reinterpret_cast<Real *>(p.vecR) + ((size_t)s * kVecR + which) * p.ld;
@@ -675,58 +679,161 @@ __global__ void __launch_bounds__(256) k_moments(Params p)
     }
 }
 
-// Sum of the G per-CTA partials in FP64 in a fixed order.  Block = 32 elements x 8
-// groups: group gg adds partials g = gg, gg + 8, ... in order, then the 8 group sums are
-// added in group order.  cg_mode = 0: vectors 0..nvec-1 into v64 slots dst0..; cg_mode = 1
-// (CG product, converged queries skipped): q = sum / W - S (S.p) + lambda p into slot 5 and
-// the block's share of p.q into bpart.  Grid (ceil(ld / 32), Q).
-template <typename Real>
-__global__ void __launch_bounds__(256) k_reduce_partials(Params p, int nvec, int dst0, int cg_mode)
+// Sum of the G per-CTA partial vectors in a fixed order.  Block = 32 lanes x GR groups
+// (GR = blockDim.x / 32 >= 4) over a tile of kRedTile = 128 elements; lane l owns the four
+// consecutive elements 4l..4l+3 of the tile.  Group gg adds partials g = gg, gg + GR, ...
+// in order (loads issued eight at a time), then thread t < 128 adds the GR group sums of
+// element t in group order.  With FP32 partials every addition is compensated (Neumaier
+// 1974): the running sum and its error term stay in FP32 and only the final s + c is
+// widened to FP64.  FP64 partials are added in FP64.
+//   cg_mode = 0: vectors 0..nvec-1 into v64 slots dst0..
+//   cg_mode = 1: the product of the CG pass (queries already converged skip):
+//       w = sum / W - S (S . r) + lambda r   (Gamma_c r + lambda r, Eq. 3.19's operator)
+//     into slot 5 and this block's share of w . r into bpart; the last block of the query
+//     to finish adds the shares (delta = w . r) and derives the scalars of the pass of
+//     k_cg_update (Chronopoulos and Gear 1989): with gamma = r . r,
+//       t = 0: beta = 0, a = gamma / delta;
+//       t > 0: beta = gamma / gamma_prev, a = gamma / (delta - beta gamma / a_prev).
+// Grid (nblk, Q), nblk = ceil(ld / kRedTile).
+template <typename Real> struct RedAcc {
+    double s;
+    __device__ __forceinline__ void init() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void merge(double x, double) { s += x; }
+    __device__ __forceinline__ double hi() const { return s; }
+    __device__ __forceinline__ double lo() const { return 0.0; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct RedAcc<float> {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.0f; c = 0.0f; }
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x)
+                                               : __fadd_rn(__fsub_rn(x, t), s));
+        s = t;
+    }
+    __device__ __forceinline__ void merge(float xs, float xc)
+    {
+        add(xs);
+        c = __fadd_rn(c, xc);
+    }
+    __device__ __forceinline__ float hi() const { return s; }
+    __device__ __forceinline__ float lo() const { return c; }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename Real> struct Quad {
+    Real v[4];
+};
+template <typename Real> __device__ __forceinline__ Quad<Real> ld_quad(const Real *p)
 {
-    __shared__ double sm[8][33];
+    Quad<Real> q;
+    if constexpr (sizeof(Real) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        q.v[0] = t.x; q.v[1] = t.y; q.v[2] = t.z; q.v[3] = t.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2 *>(p);
+        const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+    }
+    return q;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(512) k_reduce_partials(Params p, int nvec, int dst0, int cg_mode)
+{
+    using Acc = RedAcc<Real>;
+    using Lo = decltype(Acc{}.lo());
+    constexpr int kB = 8;  // loads in flight per lane
+    __shared__ Real sh_s[16][kRedTile];
+    __shared__ Lo sh_c[16][kRedTile];
+    __shared__ double sh_w[4];
+    __shared__ int last_sh;
     const int s = blockIdx.y;
-    if (cg_mode && p.st[s].done) return;
-    const int ii = threadIdx.x & 31, gg = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + ii;
+    SolveState &st = p.st[s];
+    if (cg_mode && st.done) return;
+    const int lane = threadIdx.x & 31, gg = threadIdx.x >> 5, GR = blockDim.x >> 5;
+    const int e0 = blockIdx.x * kRedTile + 4 * lane;  // first element of this lane
+    const bool in = e0 < p.ld;                        // ld is a multiple of 4
     const WS<Real> ws(p);
-    const size_t stride = (size_t)kPartVecs * p.ld;
+    const size_t stride = (size_t)kPartVecs * p.ld * GR;   // between this group's partials
     for (int v = 0; v < nvec; ++v) {
-        double acc = 0.0;
-        if (i < p.ld) {
-            const Real *src = ws.part(s, 0, v) + i;
-            int g = gg;
-            for (; g + 24 < p.G; g += 32) {
-                Real t[4];
+        Acc acc[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) t[u] = src[(size_t)(g + 8 * u) * stride];
+        for (int e = 0; e < 4; ++e) acc[e].init();
+        if (in) {
+            const Real *src = ws.part(s, gg, v) + e0;
+            for (int g0 = gg; g0 < p.G; g0 += kB * GR, src += kB * stride) {
+                Quad<Real> t[kB];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc += (double)t[u];
+                for (int u = 0; u < kB; ++u)
+                    if (g0 + u * GR < p.G) t[u] = ld_quad(src + u * stride);
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    if (g0 + u * GR < p.G) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e].add(t[u].v[e]);
+                    }
+                }
             }
-            for (; g < p.G; g += 8) acc += (double)src[(size_t)g * stride];
         }
-        sm[gg][ii] = acc;
-        __syncthreads();
-        if (gg == 0) {
-            double tot = 0.0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) tot += sm[k][ii];
+        for (int e = 0; e < 4; ++e) {
+            sh_s[gg][4 * lane + e] = acc[e].hi();
+            sh_c[gg][4 * lane + e] = acc[e].lo();
+        }
+        __syncthreads();
+        if (threadIdx.x < kRedTile) {
+            const int t = threadIdx.x, i = blockIdx.x * kRedTile + t;
+            Acc tot;
+            tot.init();
+            for (int k = 0; k < GR; ++k) tot.merge(sh_s[k][t], sh_c[k][t]);
+            const double sum = tot.value();
             if (!cg_mode) {
-                if (i < p.ld) ws.v64(s, dst0 + v)[i] = tot;
+                if (i < p.ld) ws.v64(s, dst0 + v)[i] = sum;
             } else {
-                const SolveState &st = p.st[s];
-                double pq = 0.0;
+                double wr = 0.0;
                 if (i < p.ld) {
-                    const double pi = ws.v64(s, 2)[i];
-                    const double qi = tot * st.invW - ws.v64(s, 3)[i] * st.sp + st.lambda * pi;
-                    ws.v64(s, 5)[i] = qi;
-                    pq = pi * qi;
+                    const double ri = ws.v64(s, 1)[i];
+                    const double wi = sum * st.invW - ws.v64(s, 3)[i] * st.sp + st.lambda * ri;
+                    ws.v64(s, 5)[i] = wi;
+                    wr = wi * ri;
                 }
 #pragma unroll
-                for (int o = 16; o; o >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, o);
-                if (ii == 0) p.bpart[(size_t)s * p.nblk + blockIdx.x] = pq;
+                for (int o = 16; o; o >>= 1) wr += __shfl_xor_sync(0xffffffffu, wr, o);
+                if (lane == 0) sh_w[t >> 5] = wr;
             }
         }
         __syncthreads();
+    }
+    if (!cg_mode) return;
+    double *bp = p.bpart + (size_t)s * p.nblk * kBpart;
+    if (threadIdx.x == 0) {
+        bp[(size_t)blockIdx.x * kBpart] = ((sh_w[0] + sh_w[1]) + sh_w[2]) + sh_w[3];
+        __threadfence();
+        last_sh = atomicAdd(&st.arrive_q, 1) == p.nblk - 1;
+    }
+    __syncthreads();
+    if (!last_sh || threadIdx.x >= 32) return;
+    __threadfence();
+    double dl = 0.0;
+    for (int b = lane; b < p.nblk; b += 32) dl += __ldcg(bp + (size_t)b * kBpart);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    if (lane == 0) {
+        const double gam = st.rr;
+        double beta = 0.0, den = dl;
+        if (st.iters > 0) {
+            beta = gam / st.rr_prev;
+            den = dl - beta * gam / st.cg_alpha;
+        }
+        const double a = gam / den;
+        st.cg_beta = beta;
+        st.cg_step = a;
+        st.cg_ok = (den > 0.0 && isfinite(a)) ? 1 : 0;
+        st.arrive_q = 0;
     }
 }
 
@@ -751,7 +858,8 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
         x[i] = 0.0;
         xR[i] = Real(0);
         pR[i] = Real(0);
-        for (int v = 1; v < kVec64 - 1; ++v) ws.v64(s, v)[i] = 0.0;
+        for (int v = 1; v < kVec64; ++v)
+            if (v != 6) ws.v64(s, v)[i] = 0.0;
         if (s == 0) ws.thetaR()[i] = (Real)th;
         if (i < p.d) {
             acc[0] += cos(xi);
@@ -856,75 +964,107 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     }
 }
 
-// One CG step after the product reduction (q in slot 5, p.q by reduction block):
-//   a = rr/(p.q),  x += a p,  r -= a q,  p = r + (rr'/rr) p.
-// In a CUDA graph (use_h = 1) the last CTA to finish sets the while-loop condition: 1
-// while some query has not converged and fewer than cg_max_iter passes ran.
+// One pass of the CG iteration of Chronopoulos and Gear (1989), the form of conjugate
+// gradients with a single reduction phase per iteration.  The product w = A r and the
+// scalars beta, a of the pass come from k_reduce_partials; here
+//   p = r + beta p,  s = w + beta s (= A p),  x += a p,  r -= a s,
+// one warp per tile of kRedTile elements (four consecutive elements per lane), with the
+// tile's shares of S . r and r . r for the next pass.  The last block of the query to
+// finish (arrival counter) adds those shares, stores the new state and tests convergence;
+// a query that is done stays done, so every block of a launch sees the same state.  Each
+// FP64 warp instruction occupies the SM's FP64 pipe for many cycles on this part, so the
+// scalar work is done once per query (in the reduction) rather than once per block.  In a
+// CUDA graph (use_h = 1) the last query to finish sets the while-loop condition: 1 while
+// some query has not converged and fewer than cg_max_iter passes ran.  Grid (nblk, Q).
 template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_cg_step(Params p, cudaGraphConditionalHandle h,
-                                                         int use_h)
+__global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditionalHandle h, int use_h)
 {
-    __shared__ double sm[32 * 4];
-    __shared__ double pq_sh;
-    const int s = blockIdx.x;
+    const int s = blockIdx.y, lane = threadIdx.x;
     SolveState &st = p.st[s];
-    if (!st.done) {
+    bool global_arrive = false;
+    if (st.done) {
+        global_arrive = blockIdx.x == 0;   // one block answers for a finished query
+    } else {
         const WS<Real> ws(p);
         double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
-               *q = ws.v64(s, 5);
-        Real *pR = ws.vR(s, 0);
-        const double rr = st.rr;
-        if (threadIdx.x == 0) {
-            double a = 0.0;
-            for (int b = 0; b < p.nblk; ++b) a += p.bpart[(size_t)s * p.nblk + b];
-            pq_sh = a;
-        }
-        __syncthreads();
-        const double pq = pq_sh;
-        if (!(pq > 0.0) || !isfinite(pq)) {  // breakdown: keep the current iterate
-            if (threadIdx.x == 0) {
-                st.done = 1;
-                if (!(rr <= p.cg_tol2 * st.rhs2) && st.status == 0) st.status = FBSDE_ERR_CG;
-            }
-        } else {
-            const double step = rr / pq;
-            double b1[1] = {0.0};
-            #pragma unroll 4
-            for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-                x[i] += step * pp[i];
-                r[i] -= step * q[i];
-                b1[0] += r[i] * r[i];
-            }
-            block_sum(b1, sm);
-            const double rr_new = b1[0], beta = rr_new / rr;
-            double c1[1] = {0.0};
-            #pragma unroll 4
-            for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-                const double pi = r[i] + beta * pp[i];
+               *w = ws.v64(s, 5), *sv = ws.v64(s, 7);
+        Real *rR = ws.vR(s, 0);
+        double *bp = p.bpart + (size_t)s * p.nblk * kBpart;
+        const int t = st.iters, ok = st.cg_ok;
+        const double beta = st.cg_beta, a = st.cg_step, gam = st.rr;
+        const int i0 = blockIdx.x * kRedTile + 4 * lane;
+        double sr = 0.0, rr = 0.0;
+        if (ok && i0 < p.ld) {  // ld is a multiple of 4
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = i0 + e;
+                const double ri = r[i], wi = w[i];
+                const double pi = t > 0 ? ri + beta * pp[i] : ri;
+                const double si = t > 0 ? wi + beta * sv[i] : wi;
                 pp[i] = pi;
-                pR[i] = (Real)pi;
-                c1[0] += S[i] * pi;
+                sv[i] = si;
+                x[i] += a * pi;
+                const double rn = ri - a * si;
+                r[i] = rn;
+                rR[i] = (Real)rn;
+                sr += S[i] * rn;
+                rr += rn * rn;
             }
-            block_sum(c1, sm);
-            if (threadIdx.x == 0) {
-                st.rr = rr_new;
-                st.sp = c1[0];
-                st.iters += 1;
-                st.cg_total += 1;
-                const bool conv = rr_new <= p.cg_tol2 * st.rhs2;
-                if (conv) st.done = 1;
-                else if (st.iters >= p.cg_max_iter) {
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        }
+        int last = 0;
+        if (lane == 0) {
+            bp[(size_t)blockIdx.x * kBpart + 1] = sr;
+            bp[(size_t)blockIdx.x * kBpart + 2] = rr;
+            __threadfence();
+            last = atomicAdd(&st.arrive_q, 1) == p.nblk - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            double c0 = 0.0, c1 = 0.0;
+            for (int b = lane; b < p.nblk; b += 32) {
+                c0 += __ldcg(bp + (size_t)b * kBpart + 1);
+                c1 += __ldcg(bp + (size_t)b * kBpart + 2);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            }
+            if (lane == 0) {
+                st.arrive_q = 0;
+                if (!ok) {  // breakdown: keep the current iterate
                     st.done = 1;
-                    st.cg_exhausted += 1;
-                    if (st.status == 0) st.status = FBSDE_ERR_CG;
+                    if (!(gam <= p.cg_tol2 * st.rhs2) && st.status == 0) st.status = FBSDE_ERR_CG;
+                } else {
+                    st.rr_prev = gam;
+                    st.cg_alpha = a;
+                    st.rr = c1;
+                    st.sp = c0;
+                    st.iters = t + 1;
+                    st.cg_total += 1;
+                    if (c1 <= p.cg_tol2 * st.rhs2) {
+                        st.done = 1;
+                    } else if (t + 1 >= p.cg_max_iter) {
+                        st.done = 1;
+                        st.cg_exhausted += 1;
+                        if (st.status == 0) st.status = FBSDE_ERR_CG;
+                    }
                 }
+                global_arrive = true;
             }
         }
     }
-    if (use_h && threadIdx.x == 0) {
+    if (use_h && global_arrive && lane == 0) {
         __threadfence();
         const int arrived = atomicAdd(&p.st[0].arrive, 1);
         if (arrived == p.Q - 1) {
+            __threadfence();
             p.st[0].arrive = 0;
             const int count = ++p.st[0].loop_iter;
             bool active = false;
@@ -986,25 +1126,14 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     }
 }
 
-// Condition of the CUDA-graph while loop around the CG iterations (default value 1, so
-// the body runs once before the first check): after each pass it stays 1 while some
-// query has not converged and fewer than cg_max_iter passes ran.  reset = 1 (outside
-// the loop) zeroes the pass counter, kept in the first query's state.
-template <typename Real>
-__global__ void k_cg_check(Params p, cudaGraphConditionalHandle h, int reset)
+// Before the CUDA-graph while loop around the CG passes (its condition defaults to 1, so
+// the body runs once before k_cg_update first sets it): zero the pass counter and the
+// arrival counter, kept in the first query's state.
+template <typename Real> __global__ void k_cg_reset(Params p)
 {
     if (threadIdx.x != 0) return;
-    int &count = p.st[0].loop_iter;
-    if (reset) {
-        count = 0;
-        p.st[0].arrive = 0;
-        return;
-    }
-    count += 1;
-    bool active = false;
-    for (int s = 0; s < p.Q && !active; ++s) active = p.st[s].done == 0;
-    if (count >= p.cg_max_iter) active = false;
-    cudaGraphSetConditional(h, active ? 1u : 0u);
+    p.st[0].loop_iter = 0;
+    p.st[0].arrive = 0;
 }
 
 // Trace copy of the forward-sweep end state (X_N - x0 and Y_N) into FP64 arrays.

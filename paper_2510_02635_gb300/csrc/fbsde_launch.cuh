@@ -68,8 +68,8 @@ template <typename Real>
 cudaError_t Launch<Real>::reduce(const Params &p, const Layout &L, int nvec, int dst0,
                                  int skip_done, cudaStream_t s)
 {
-    dev::k_reduce_partials<Real><<<dim3((L.ld + 31) / 32, L.Q), 256, 0, s>>>(p, nvec, dst0,
-                                                                             skip_done);
+    dev::k_reduce_partials<Real><<<dim3(L.nblk, L.Q), 32 * L.red_groups, 0, s>>>(p, nvec, dst0,
+                                                                                 skip_done);
     return cudaGetLastError();
 }
 
@@ -106,10 +106,10 @@ cudaError_t Launch<Real>::moments_finalize(const Params &p, const Layout &L, int
 }
 
 template <typename Real>
-cudaError_t Launch<Real>::cg_step(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
-                                  int use_h, cudaStream_t s)
+cudaError_t Launch<Real>::cg_update(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
+                                    int use_h, cudaStream_t s)
 {
-    dev::k_cg_step<Real><<<L.Q, kFinThreads, 0, s>>>(p, h, use_h);
+    dev::k_cg_update<Real><<<dim3(L.nblk, L.Q), 32, 0, s>>>(p, h, use_h);
     return cudaGetLastError();
 }
 
@@ -120,11 +120,9 @@ cudaError_t Launch<Real>::cg_post(const Params &p, const Layout &L, cudaStream_t
     return cudaGetLastError();
 }
 
-template <typename Real>
-cudaError_t Launch<Real>::cg_check(const Params &p, cudaGraphConditionalHandle h, int reset,
-                                   cudaStream_t s)
+template <typename Real> cudaError_t Launch<Real>::cg_reset(const Params &p, cudaStream_t s)
 {
-    dev::k_cg_check<Real><<<1, 32, 0, s>>>(p, h, reset);
+    dev::k_cg_reset<Real><<<1, 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -68,7 +68,7 @@ class fbsde_diag(C.Structure):
 EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_host_staging_bytes", "fbsde_diagnostics", "fbsde_philox4x32_10",
            "fbsde_normals", "fbsde_status_string", "fbsde_abi_version",
-           "fbsde_profile_start", "fbsde_profile_stop", "fbsde_kernel_name",
+           "fbsde_profile_start", "fbsde_profile_select", "fbsde_profile_stop", "fbsde_kernel_name",
            "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics"]
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_status_string.restype = C.c_char_p
         lib.fbsde_profile_start.argtypes = [I32]
         lib.fbsde_profile_start.restype = C.c_int
+        lib.fbsde_profile_select.argtypes = [C.c_uint32]
+        lib.fbsde_profile_select.restype = C.c_int
         lib.fbsde_profile_stop.argtypes = [C.POINTER(fbsde_kernel_stats)]
         lib.fbsde_profile_stop.restype = C.c_int
         lib.fbsde_kernel_name.argtypes = [C.c_int]
@@ -250,6 +252,16 @@ def fbsde_status_string(status: int) -> str:
 
 def fbsde_profile_start(max_timed_launches: int) -> int:
     return int(load_library().fbsde_profile_start(int(max_timed_launches)))
+
+
+def fbsde_profile_select(families) -> int:
+    """Time only the named kernel families (e.g. ["matvec"]); the others are counted."""
+    lib = load_library()
+    names = [lib.fbsde_kernel_name(f).decode() for f in range(FBSDE_NUM_KERNELS)]
+    mask = 0
+    for fam in families:
+        mask |= 1 << names.index(fam)
+    return int(lib.fbsde_profile_select(mask))
 
 
 def fbsde_profile_stop() -> dict:
