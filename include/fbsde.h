@@ -135,7 +135,12 @@ FBSDE_API size_t fbsde_workspace_bytes(const fbsde_problem *P, int32_t Q);
 
 /*
  * Algorithm 1 for Q query points at once (independent solves, one particle cloud
- * each).  Query q uses the Philox stream of solve index solve_index0 + q.
+ * each).  Query q uses the Philox stream of solve index solve_index0 + q.  The Brownian
+ * path of each particle (Eq. 2.7 with mu = 0, so X_k = x0 + sigma W(t_k)) is drawn
+ * backwards from its end point by the Brownian bridge: W(T) = sqrt(T) xi_N and, for
+ * k = N-1..1, W(t_k) = (k/(k+1)) W(t_{k+1}) + sqrt(dt k/(k+1)) xi_k, W(0) = 0.  Its
+ * increments are independent N(0, dt I), the law Eq. 2.7 gives them; the forward sweep
+ * needs one normal per coordinate and the backward sweep one per level.
  *   x0        device [Q][d]  query points
  *   seed      Philox4x32-10 key of the Brownian increments
  *   u0        device [Q]     output u(0, x0_q)
@@ -222,9 +227,9 @@ FBSDE_API int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *w
 FBSDE_API int fbsde_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                         fbsde_stream_t stream);
 
-/* The standard normals xi_{s,k,j,i} behind the increments Delta W_k^j = sqrt(dt) xi
-   of Eq. (2.7), exactly as the solver draws them: particles j0..j0+nj-1 of level k
-   of solve s, dimensions 0..d-1.  out: device [nj][d] of float (FBSDE_FP32) or
+/* The standard normals xi_{s,k,j,i} of the Brownian paths of Eq. (2.7), exactly as
+   the solver draws them (k = N: the end point W(T); 1 <= k < N: the bridge step to
+   level k): particles j0..j0+nj-1 of level k of solve s, dimensions 0..d-1.  out: device [nj][d] of float (FBSDE_FP32) or
    double (FBSDE_FP64). */
 FBSDE_API int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int32_t nj, int32_t d,
                   int32_t precision, void *out, fbsde_stream_t stream);

@@ -102,6 +102,9 @@ def _load():
             lib.orc_adjoint.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, _dp,
                                         _dp, _dp]
             lib.orc_adjoint.restype = C.c_int
+            lib.orc_path.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, C.c_int64,
+                                     _dp]
+            lib.orc_path.restype = C.c_int
             lib.orc_g_grad.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
             lib.orc_g_grad.restype = None
             lib.orc_f_grads.argtypes = [C.POINTER(_Problem), C.c_double, _dp, C.c_double, _dp,
@@ -175,9 +178,22 @@ def uniform(x: int) -> float:
 
 
 def normals(seed: int, s: int, k: int, j: int, d: int) -> np.ndarray:
-    """xi_{s,k,j,0..d-1}: the standard normals behind Delta W_k^j of particle j (Eq. 2.7)."""
+    """xi_{s,k,j,0..d-1}: the standard normals of particle j at level k (k = N: the end
+    point of its Brownian path, 1 <= k < N: the bridge step to level k)."""
     out = np.zeros(d, dtype=np.float64)
     _load().orc_normals(seed, s, k, j, d, _ptr(out))
+    return out
+
+
+def path(prob: Problem, x0, seed: int, s: int, j: int) -> np.ndarray:
+    """Positions X_0..X_N ([N+1, d]) of particle j of solve s: the Brownian path of
+    Eq. 2.7 drawn backwards by the Brownian bridge, as the solve and the adjoint draw it."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    out = np.zeros((prob.N + 1, prob.d))
+    ps = prob.c_struct()
+    st = _load().orc_path(C.byref(ps), _ptr(x0), seed, s, j, _ptr(out))
+    if st != 0:
+        raise RuntimeError(f"orc_path: status {st}")
     return out
 
 

@@ -18,8 +18,16 @@
  *            with drift mu = 0 and a constant scalar diffusion sigma (all problems
  *            below), so the anchor of every regression is a_k = x0.
  *   grid     (Sec. 2.2): dt = T/N, t_k = k dt.
- *   forward  (2.7), Algorithm 1: X_0^j = x0, X_{k+1}^j = X_k^j + sigma dW_k^j,
- *            dW_k^j = sqrt(dt) xi_{s,k,j}, Y_N^j = g(X_N^j).
+ *   forward  (2.7), Algorithm 1: X_0^j = x0, X_{k+1}^j = X_k^j + sigma dW_k^j, so with
+ *            mu = 0 the increments telescope to X_N^j = x0 + sigma W^j(T);
+ *            Y_N^j = g(X_N^j).  The Brownian path W^j at the grid times is drawn
+ *            backwards from its end point by the Brownian bridge (Levy's construction;
+ *            Glasserman, Monte Carlo Methods in Financial Engineering, 2004, Sec. 3.1):
+ *              W(T) = sqrt(T) xi_{s,N,j},
+ *              W(t_k) = (t_k/t_{k+1}) W(t_{k+1}) + sqrt(t_k dt / t_{k+1}) xi_{s,k,j},
+ *            k = N-1..1, W(0) = 0.  Its increments W(t_{k+1}) - W(t_k) are independent
+ *            N(0, dt I), the law (2.7) gives dW_k, so the estimator is the same random
+ *            variable in law as with increments drawn in forward order.
  *   backward (2.6)/(2.8), Algorithm 1, for k = N-1..0:
  *            weighted local linear regression (2.10)-(2.15) of Y_{k+1}^j on
  *            D_j = X_{k+1}^j - a_k with Gaussian kernel weights (2.11), Remark 2.3,
@@ -43,8 +51,10 @@
  *   - ridge lambda = ridge_rel * tr(Gamma_c)/d on the slope only;
  *   - unpreconditioned CG from zero, stopping at ||r|| <= cg_tol ||rhs||;
  *   - X_0^j = x0 exactly at k = 0 (Algorithm 1 starts every path at x);
- *   - the backward sweep recovers X_k from X_{k+1} by subtracting the same
- *     regenerated increment (the forward recursion (2.7) solved for X_k).
+ *   - the backward sweep recovers X_k from X_{k+1} by the bridge step above,
+ *     X_k = x0 + (t_k/t_{k+1}) (X_{k+1} - x0) + sigma sqrt(t_k dt / t_{k+1}) xi_{s,k,j}:
+ *     nothing per level is stored, and the forward sweep draws one normal per
+ *     dimension instead of N.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11) with counter (q, j, k, s), key (seed lo,
@@ -151,6 +161,57 @@ void orc_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j, int32_t d, d
         for (int m = 0; m < 4 && 4 * q + m < d; ++m)
             xi[4 * q + m] = z[m];
     }
+}
+
+/*
+ * Particle positions of the Brownian path of (2.7) with mu = 0, drawn backwards by the
+ * Brownian bridge (Levy's construction; Glasserman 2004, Sec. 3.1).  With W(0) = 0 the
+ * conditional law of W(t_k) given W(t_{k+1}) is
+ *   N((t_k/t_{k+1}) W(t_{k+1}), t_k (t_{k+1} - t_k)/t_{k+1} I),
+ * so on positions X = x0 + sigma W:
+ *   path_end:  X_N = x0 + sigma sqrt(T) xi_{s,N,j};
+ *   path_step: X_k = x0 + (k/(k+1)) (X_{k+1} - x0) + sigma sqrt(dt k/(k+1)) xi_{s,k,j},
+ *              1 <= k < N, and X_0 = x0 (k = 0).
+ * xi is scratch of d doubles; Xk may alias Xn.
+ */
+static void path_end(const orc_problem *P, const double *x0, uint64_t seed, uint32_t s,
+                     int64_t j, double *XN, double *xi)
+{
+    const int d = P->d;
+    const double sT = P->sigma * sqrt(P->T);
+    orc_normals(seed, s, (uint32_t)P->N, (uint32_t)j, d, xi);
+    for (int i = 0; i < d; ++i) XN[i] = x0[i] + sT * xi[i];
+}
+
+static void path_step(const orc_problem *P, int k, const double *x0, uint64_t seed, uint32_t s,
+                      int64_t j, const double *Xn, double *Xk, double *xi)
+{
+    const int d = P->d;
+    if (k == 0) {
+        for (int i = 0; i < d; ++i) Xk[i] = x0[i];
+        return;
+    }
+    const double dt = P->T / P->N;
+    const double ca = (double)k / (double)(k + 1);
+    const double cb = P->sigma * sqrt(dt * (double)k / (double)(k + 1));
+    orc_normals(seed, s, (uint32_t)k, (uint32_t)j, d, xi);
+    for (int i = 0; i < d; ++i) Xk[i] = x0[i] + ca * (Xn[i] - x0[i]) + cb * xi[i];
+}
+
+/* The whole path X_0..X_N of particle j (out[(N+1) d], level-major), by the two steps
+ * that orc_solve and orc_adjoint use. */
+int orc_path(const orc_problem *P, const double *x0, uint64_t seed, uint32_t s, int64_t j,
+             double *out)
+{
+    const int d = P->d, N = P->N;
+    if (d < 1 || N < 1 || !(P->T > 0.0) || !(P->sigma > 0.0) || j < 0) return ORC_ERR_ARG;
+    double *xi = (double *)malloc(sizeof(double) * d);
+    if (!xi) return ORC_ERR_NOMEM;
+    path_end(P, x0, seed, s, j, out + (size_t)N * d, xi);
+    for (int k = N - 1; k >= 0; --k)
+        path_step(P, k, x0, seed, s, j, out + (size_t)(k + 1) * d, out + (size_t)k * d, xi);
+    free(xi);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -444,7 +505,6 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
     if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta)
         return ORC_ERR_ARG;
     const double dt = P->T / N;
-    const double sdt = P->sigma * sqrt(dt);
     const size_t Md = (size_t)M * (size_t)d;
 
     double *X = (double *)malloc(sizeof(double) * Md);
@@ -466,7 +526,7 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
     struct timespec tw0, tw1, tw2;
     clock_gettime(CLOCK_MONOTONIC, &tw0);
 
-    /* forward sweep (2.7): X_0 = x0, X_{k+1} = X_k + sigma sqrt(dt) xi_k */
+    /* forward sweep (2.7) with mu = 0: X_N = x0 + sigma W(T), W(T) = sqrt(T) xi_N */
 #pragma omp parallel
     {
         int id = 0;
@@ -477,11 +537,7 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
 #pragma omp for schedule(static)
         for (int64_t j = 0; j < M; ++j) {
             double *Xj = X + j * (int64_t)d;
-            for (int i = 0; i < d; ++i) Xj[i] = x0[i];
-            for (int k = 0; k < N; ++k) {
-                orc_normals(seed, solve_index, (uint32_t)k, (uint32_t)j, d, xi);
-                for (int i = 0; i < d; ++i) Xj[i] += sdt * xi[i];
-            }
+            path_end(P, x0, seed, solve_index, j, Xj, xi);
             Y[j] = orc_g(P, Xj); /* terminal condition, Algorithm 1 */
         }
     }
@@ -522,12 +578,7 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
 #pragma omp for schedule(static)
             for (int64_t j = 0; j < M; ++j) {
                 double *Xj = X + j * (int64_t)d;
-                if (k == 0) {
-                    for (int i = 0; i < d; ++i) Xj[i] = x0[i];
-                } else {
-                    orc_normals(seed, solve_index, (uint32_t)k, (uint32_t)j, d, xi);
-                    for (int i = 0; i < d; ++i) Xj[i] -= sdt * xi[i];
-                }
+                path_step(P, k, x0, seed, solve_index, j, Xj, Xj, xi); /* X_k from X_{k+1} */
                 double pred = alpha;
                 for (int i = 0; i < d; ++i) pred += ax[i] * (Xj[i] - x0[i]);
                 double feat = orc_f_feature(P, t_k, Xj, z);
@@ -692,7 +743,7 @@ int orc_adjoint(const orc_problem *P, const double *x0, uint64_t seed, uint32_t 
     const int64_t M = P->M;
     if (d < 1 || N < 1 || M < 2 || !(P->T > 0.0) || !(P->sigma > 0.0)) return ORC_ERR_ARG;
     if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta) return ORC_ERR_ARG;
-    const double dt = P->T / N, sdt = P->sigma * sqrt(dt);
+    const double dt = P->T / N;
     const size_t Md = (size_t)M * d;
     double *X = (double *)malloc(sizeof(double) * Md * (N + 1));     /* X_k, k = 0..N */
     double *Yl = (double *)malloc(sizeof(double) * (size_t)M * (N + 1)); /* Y_k        */
@@ -715,20 +766,18 @@ int orc_adjoint(const orc_problem *P, const double *x0, uint64_t seed, uint32_t 
     double *z = vec, *ab = vec + d, *rhs = vec + 2 * d, *v = vec + 3 * d, *fx = vec + 4 * d,
            *fz = vec + 5 * d, *xb = vec + 6 * d, *tb = vec + 7 * d;
 
-    /* ---- forward sweep (2.7), stored for every level */
+    /* ---- the particle paths of every level (the same bridge as orc_solve) */
 #pragma omp parallel
     {
         double *xi = (double *)malloc(sizeof(double) * d);
 #pragma omp for schedule(static)
         for (int64_t j = 0; j < M; ++j) {
-            for (int i = 0; i < d; ++i) X[j * (int64_t)d + i] = x0[i];
-            for (int k = 0; k < N; ++k) {
-                const double *Xk = X + (size_t)k * Md + j * (int64_t)d;
-                double *Xn = X + (size_t)(k + 1) * Md + j * (int64_t)d;
-                orc_normals(seed, solve_index, (uint32_t)k, (uint32_t)j, d, xi);
-                for (int i = 0; i < d; ++i) Xn[i] = Xk[i] + sdt * xi[i];
-            }
-            Yl[(size_t)N * M + j] = orc_g(P, X + (size_t)N * Md + j * (int64_t)d);
+            double *XN = X + (size_t)N * Md + j * (int64_t)d;
+            path_end(P, x0, seed, solve_index, j, XN, xi);
+            for (int k = N - 1; k >= 0; --k)
+                path_step(P, k, x0, seed, solve_index, j, X + (size_t)(k + 1) * Md + j * (int64_t)d,
+                          X + (size_t)k * Md + j * (int64_t)d, xi);
+            Yl[(size_t)N * M + j] = orc_g(P, XN);
         }
         free(xi);
     }

@@ -326,8 +326,8 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
 
 // Reverse sweep (see fbsde_adjoint.cuh): the primal is re-run with its tape recorded,
 // then for k = 0..N-1 the adjoint solve of level k, the per-particle adjoint and the
-// column sums, walking the particle rows forward from Delta_1 by regenerating the
-// increments.
+// column sums, walking the particle rows up from Delta_1 by inverting the Brownian-bridge
+// steps with the regenerated normals.
 template <typename Real>
 cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const double *theta,
                         const double *ubar, double *x0bar, double *thetabar, char *base,
@@ -365,7 +365,7 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_colsum(p, L, mb, terminal ? mode_c : 0, s));
         FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_finalize(p, L, s));
-        if (!terminal) {  // rows Delta_{k+1} -> Delta_{k+2}, regenerating increment k+1
+        if (!terminal) {  // rows Delta_{k+1} -> Delta_{k+2}: the bridge step of level k+1 inverted
             Params q = p;
             q.level = k + 1;
             q.walk = +1;

@@ -14,6 +14,7 @@
 // ld = d rounded up to a multiple of 4 (16-byte rows for float and 32-byte rows for
 // double); the padding of every row and vector is kept at zero.
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <algorithm>
 #include <cstdint>
@@ -62,6 +63,7 @@ struct Params {
         newton_level, Q, nseg, GP, GS, mv_rows, mv_stages, walk, nblk;
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
+    double wa, wb;  // path step of the row kernels: Delta <- wa Delta + wb xi (set per launch)
     uint32_t key0, key1, solve0;
     // workspace
     void *delta;

@@ -382,7 +382,9 @@ template <typename T, int NV> __device__ __forceinline__ void warp_sum(T (&v)[NV
 // no shared memory, coalesced 512-byte accesses per warp instruction.
 // ---------------------------------------------------------------------------
 
-// Forward sweep (2.7): Delta_N^j = sum_k sigma sqrt(dt) xi_{s,k,j} (X_0 = x0), stored;
+// Forward sweep (2.7) with mu = 0: the increments telescope to Delta_N^j = sigma W^j(T),
+// and the Brownian path is drawn backwards from its end point (Brownian bridge, see
+// k_update), so Delta_N^j = sigma sqrt(T) xi_{s,N,j} (wb = sigma sqrt(T)), stored;
 // segment sums of (|Delta|^2, terminal feature of g at x0 + Delta).
 template <typename Real, int VPT>
 __global__ void __launch_bounds__(256) k_forward(Params p)
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(256) k_forward(Params p)
     const int nch = p.ld / E;
     const long long items = (long long)p.Q * p.M * p.nseg;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const Real sdt = (Real)p.sdt;
+    const Real wb = (Real)p.wb;
     const bool need_theta = p.kind == FBSDE_HJB_LOGQUAD || p.kind == FBSDE_AFFINE_TEST;
     const Real *thr = ws.thetaR();
     for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
@@ -410,14 +412,10 @@ __global__ void __launch_bounds__(256) k_forward(Params p)
         for (int v = 0; v < VPT; ++v) {
             const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) {
-                Chunk<Real> dl;
-                zero(dl);
-                for (int k = 0; k < p.N; ++k) {
-                    const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
-                                                       (uint32_t)k, sidx, p.key0, p.key1, p.d);
+                Chunk<Real> dl = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
+                                              (uint32_t)p.N, sidx, p.key0, p.key1, p.d);
 #pragma unroll
-                    for (int e = 0; e < E; ++e) dl.v[e] += sdt * z.v[e];
-                }
+                for (int e = 0; e < E; ++e) dl.v[e] *= wb;
                 const Chunk<Real> xc = ldg_chunk(x0r + c * E);
                 Chunk<Real> th;
                 if (need_theta) th = ldg_chunk(thr + c * E);
@@ -440,9 +438,11 @@ __global__ void __launch_bounds__(256) k_forward(Params p)
     }
 }
 
-// Level update (k >= 1): Delta_k = Delta_{k+1} - sigma sqrt(dt) xi_{s,k,j} in place (the
-// forward recursion (2.7) solved for X_k); segment sums of (alpha_x . Delta_k, |Delta_k|^2,
-// sum_i cos(x0_i + Delta_k,i) for the Allen-Cahn source).
+// Level update (1 <= k < N): one step of the Brownian path drawn backwards by the bridge,
+// Delta_k = a Delta_{k+1} + b xi_{s,k,j} in place (wa = a = k/(k+1), wb = b =
+// sigma sqrt(dt k/(k+1)); the reverse sweep of the adjoint runs the same step solved for
+// Delta_{k+1}); segment sums of (alpha_x . Delta_k, |Delta_k|^2, sum_i cos(x0_i + Delta_k,i)
+// for the Allen-Cahn source).
 template <typename Real, int VPT>
 __global__ void __launch_bounds__(256) k_update(Params p)
 {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
     const int k = p.level;
     const long long items = (long long)p.Q * p.M * p.nseg;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const Real wsdt = (Real)(p.walk * p.sdt);  // walk = -1: X_k from X_{k+1}; +1: forward
+    const Real wa = (Real)p.wa, wb = (Real)p.wb;
     const bool cos_feature = p.kind == FBSDE_AC_MANUFACTURED;
     for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
          it += nwarps) {
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
                 const Chunk<Real> xc = ldg_chunk(xr + c * E);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    dl[v].v[e] += wsdt * z.v[e];
+                    dl[v].v[e] = wa * dl[v].v[e] + wb * z.v[e];
                     acc[0] += xc.v[e] * dl[v].v[e];
                     acc[1] += dl[v].v[e] * dl[v].v[e];
                 }

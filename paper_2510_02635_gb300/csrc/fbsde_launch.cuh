@@ -20,25 +20,39 @@ cudaError_t Launch<Real>::setup(const Params &p, const double *x0, const double 
     return cudaGetLastError();
 }
 
-#define FBSDE_SEG_DISPATCH(KERNEL)                                                        \
+#define FBSDE_SEG_DISPATCH(KERNEL, P)                                                     \
     switch (L.seg_vpt) {                                                                  \
-    case 1: dev::KERNEL<Real, 1><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
-    case 2: dev::KERNEL<Real, 2><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
-    case 4: dev::KERNEL<Real, 4><<<L.row_blocks, 256, 0, s>>>(p); break;                 \
+    case 1: dev::KERNEL<Real, 1><<<L.row_blocks, 256, 0, s>>>(P); break;                 \
+    case 2: dev::KERNEL<Real, 2><<<L.row_blocks, 256, 0, s>>>(P); break;                 \
+    case 4: dev::KERNEL<Real, 4><<<L.row_blocks, 256, 0, s>>>(P); break;                 \
     default: return cudaErrorInvalidValue;                                                \
     }                                                                                     \
     return cudaGetLastError();
 
+// Forward sweep: Delta_N = sigma sqrt(T) xi_N, the end point of the Brownian path.
 template <typename Real>
 cudaError_t Launch<Real>::forward(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_SEG_DISPATCH(k_forward)
+    Params q = p;
+    q.wa = 0.0;
+    q.wb = p.sigma * std::sqrt(p.T);
+    FBSDE_SEG_DISPATCH(k_forward, q)
 }
 
+// Brownian-bridge step of level k = p.level (1 <= k < N): with W(0) = 0, W(t_k) given
+// W(t_{k+1}) is N((t_k/t_{k+1}) W(t_{k+1}), t_k dt / t_{k+1} I), so on the rows
+//   walk = -1: Delta_k = a Delta_{k+1} + b xi_k,  a = k/(k+1), b = sigma sqrt(dt k/(k+1));
+//   walk = +1: the same step solved for Delta_{k+1} = (Delta_k - b xi_k) / a.
 template <typename Real>
 cudaError_t Launch<Real>::update(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_SEG_DISPATCH(k_update)
+    if (p.level < 1 || p.level >= p.N) return cudaErrorInvalidValue;
+    Params q = p;
+    const double a = (double)p.level / (double)(p.level + 1);
+    const double b = p.sigma * std::sqrt(p.dt * a);
+    q.wa = p.walk < 0 ? a : 1.0 / a;
+    q.wb = p.walk < 0 ? b : -b / a;
+    FBSDE_SEG_DISPATCH(k_update, q)
 }
 
 template <typename Real>
@@ -168,7 +182,7 @@ cudaError_t Launch<Real>::adj_post(const Params &p, const Layout &L, cudaStream_
 template <typename Real>
 cudaError_t Launch<Real>::adj_rows(const Params &p, const Layout &L, cudaStream_t s)
 {
-    FBSDE_SEG_DISPATCH(k_adj_rows)
+    FBSDE_SEG_DISPATCH(k_adj_rows, p)
 }
 
 template <typename Real>

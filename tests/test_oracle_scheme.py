@@ -88,11 +88,12 @@ def test_linear_driver_equals_one_weighted_regression(c1):
     p = _prob("cos_linear_test", d, sigma, T, N, M, c1=c1, h=math.inf, ridge_rel=0.0)
     r = oracle.solve(p, x0, seed=seed, solve_index=s, keep_forward=True)
     XN = r["X_N"]
-    # forward sweep (2.7): X_N^j = x0 + sigma sqrt(dt) sum_k xi_{s,k,j}
+    # forward sweep (2.7) with mu = 0: X_N^j = x0 + sigma W^j(T), W^j(T) = sqrt(T) xi_{s,N,j}
     dt = T / N
     for j in (0, 17, M - 1):
-        inc = sum(oracle.normals(seed, s, k, j, d) for k in range(N))
-        assert np.allclose(XN[j], x0 + sigma * math.sqrt(dt) * inc, rtol=0, atol=1e-13)
+        end = oracle.normals(seed, s, N, j, d)
+        assert np.allclose(XN[j], x0 + sigma * math.sqrt(T) * end, rtol=0, atol=1e-13)
+        assert np.array_equal(oracle.path(p, x0, seed, s, j)[N], XN[j])
     gN = np.cos(XN).mean(axis=1)
     assert np.allclose(r["Y_N"], gN, rtol=0, atol=1e-15)
     design = np.hstack([np.ones((M, 1)), XN - x0])
@@ -198,3 +199,52 @@ def test_top_level_regression_uses_the_forward_cloud_and_its_spread():
     assert st == 0
     assert r["alpha"][N - 1] == pytest.approx(alpha, rel=1e-12)
     assert np.max(np.abs(r["alpha_x"][N - 1] - ax)) < 1e-12 * np.max(np.abs(ax))
+
+
+def _increments(p, x0, seed, s, M):
+    paths = np.stack([oracle.path(p, x0, seed, s, j) for j in range(M)])  # [M, N+1, d]
+    assert np.array_equal(paths[:, 0], np.broadcast_to(x0, (M, p.d)))      # X_0 = x0
+    return np.diff(paths, axis=1) / p.sigma                                 # dW_k, [M, N, d]
+
+
+def test_bridge_path_has_the_increment_law_of_the_forward_scheme():
+    """Eq. 2.7 asks for independent increments dW_k ~ N(0, dt I).  The path is drawn
+    backwards by the Brownian bridge, so check the law of its increments over many
+    particles: mean 0, variance dt at every level, no covariance between levels or
+    dimensions, Gaussian fourth moment.  A wrong bridge weight or variance (e.g. t_k in
+    place of t_k dt / t_{k+1}, or the weight 1) breaks the per-level variances."""
+    d, T, N, M, sigma = 3, 0.9, 6, 6000, 0.7
+    dt = T / N
+    p = _prob("cos_linear_test", d, sigma, T, N, M)
+    x0 = np.array([0.3, -1.1, 2.0])
+    dW = _increments(p, x0, 21, 4, M)
+    n = M * d
+    z = dW / math.sqrt(dt)                      # should be iid N(0,1)
+    se = 1.0 / math.sqrt(n)
+    for k in range(N):
+        zk = z[:, k].ravel()
+        assert abs(zk.mean()) < 5 * se, k
+        assert abs(zk.var() - 1.0) < 5 * math.sqrt(2.0) * se, k
+        assert abs(np.mean(zk ** 4) - 3.0) < 5 * math.sqrt(96.0) * se, k
+        for k2 in range(k):
+            c = np.mean(z[:, k] * z[:, k2])
+            assert abs(c) < 5 * se, (k, k2)
+    # dimensions are independent too
+    zz = z.reshape(M, N * d)
+    assert abs(np.mean(zz[:, 0] * zz[:, 1])) < 5 / math.sqrt(M)
+
+
+def test_bridge_path_ends_and_levels():
+    """W(T) = sqrt(T) xi_{s,N,j} exactly; the level-k position uses the level-k normals
+    only through the bridge step (changing the seed moves every level; the same seed
+    repeats the path bit for bit); X_0 = x0 for every particle."""
+    d, T, N = 5, 1.3, 4
+    p = _prob("cos_linear_test", d, 1.7, T, N, 8)
+    x0 = np.linspace(-1, 1, d)
+    a = oracle.path(p, x0, 3, 2, 5)
+    assert np.array_equal(a, oracle.path(p, x0, 3, 2, 5))
+    assert np.allclose(a[N], x0 + 1.7 * math.sqrt(T) * oracle.normals(3, 2, N, 5, d),
+                       rtol=0, atol=1e-15)
+    assert np.array_equal(a[0], x0)
+    b = oracle.path(p, x0, 4, 2, 5)
+    assert np.all(np.abs(a[1:] - b[1:]) > 0)
