@@ -207,12 +207,28 @@ template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV], dou
 // ---------------------------------------------------------------------------
 // Problem table (the same formulas as documented in fbsde.h).
 // ---------------------------------------------------------------------------
+// cos of a particle coordinate in the stream precision.  FP32: x - 2 pi n with
+// n = rint(x / (2 pi)) by a two-part 2 pi (Cody and Waite 1980: 6.28125 has 8 significant
+// bits, so n * 6.28125 is exact for |n| < 2^16), then the hardware cosine on [-pi, pi]
+// (absolute error below 1e-6).  The coordinates enter only through sums over d terms of
+// FP32 values (the Allen-Cahn feature sum_i cos x_i), so this is within the stream's
+// rounding; it replaces the range reduction and polynomial of the accurate cosf, which
+// dominate the instruction count of the row kernels.  FP64: cos.
+__device__ __forceinline__ float cos_stream(float x)
+{
+    const float n = rintf(x * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, x);
+    r = fmaf(-n, 1.9353071795864769e-3f, r);
+    return __cosf(r);
+}
+__device__ __forceinline__ double cos_stream(double x) { return cos(x); }
+
 // Per-element term of the terminal feature sum; x = x0_i + Delta_i.
 template <typename Real> __device__ __forceinline__ Real g_term(int kind, Real x, Real th)
 {
     switch (kind) {
     case FBSDE_AC_MANUFACTURED:
-    case FBSDE_COS_LINEAR_TEST: return cos(x);
+    case FBSDE_COS_LINEAR_TEST: return cos_stream(x);
     case FBSDE_LOGISTIC_GRAD: return x;
     case FBSDE_HJB_LOGQUAD: return th * x * x;
     case FBSDE_AFFINE_TEST: return th * x;
@@ -489,7 +505,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
                     const Chunk<Real> x0c = ldg_chunk(x0r + c * E);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if (c * E + e < p.d) acc[2] += cos(x0c.v[e] + dl[v].v[e]);
+                        if (c * E + e < p.d) acc[2] += cos_stream(x0c.v[e] + dl[v].v[e]);
                 }
                 st_chunk(drow + c * E, dl[v]);
             }
