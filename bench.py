@@ -336,18 +336,27 @@ def run_gpu(args, rank: int, world: int) -> None:
     tr = solver.solve(x0, seed=w.seed, solve_index0=sidx, trace=True)
     cg_iters = tr["cg_iters"].cpu().numpy()
     status = tr["status"]
-    # matrix-free products per step: one per CG iteration plus the warm-start product
-    # of every level below the top one
-    products = int(cg_iters.sum()) + w.Q * (w.N - 1)
+    # matrix-free products per step: one per CG pass of each query (the warm start's
+    # product comes out of the moments pass).  While the profiler times the product
+    # kernel the library launches the first FBSDE_PROFILED_EAGER_PASSES passes of every
+    # CG loop one by one (those are the bracketed launches) and the rest through a CUDA
+    # graph, so the timed launches carry min(iters, that many) products per query-level.
+    products = int(cg_iters.sum())
+    eager = fbsde.FBSDE_PROFILED_EAGER_PASSES
+    products_timed = int(np.minimum(cg_iters, eager).sum())
     mv = prof["matvec"]
     mv_ms_step = mv["total_ms"] / args.steps
     bytes_per_product = 4.0 * w.M * w.d   # one FP32 read of the particle cloud
-    achieved = bytes_per_product * products / (mv_ms_step * 1e-3) / 1e9
+    achieved = bytes_per_product * products_timed / (mv_ms_step * 1e-3) / 1e9
     peaks = _peaks()
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    launches = sum(v["launches"] for v in prof.values())
+    # kernels the library launched one by one, plus those run inside the CG-loop graphs
+    # (one reset kernel per level and three per pass beyond the eager ones)
+    beyond = np.maximum(cg_iters.reshape(w.Q, w.N).max(axis=0) - eager, 0)
+    launches = sum(v["launches"] for v in prof.values()) + \
+        args.steps * int(w.N + 3 * beyond.sum())
 
     # ---- per-family split: one more solve, every launch bracketed (outside the timed region)
     fbsde.fbsde_profile_start(1 << 18)
@@ -416,6 +425,7 @@ def run_gpu(args, rank: int, world: int) -> None:
                                            "and per CTA (profiles/matvec_traffic.txt)",
                          "algorithmic_bytes_per_product": bytes_per_product,
                          "products_per_step": products,
+                         "products_timed_per_step": products_timed,
                          "kernel_ms_per_step": mv_ms_step},
             "kernels_ms_per_step": {k: v["total_ms"] for k, v in split.items()},
             "kernels_ms_note": "one extra solve after the timed region with every launch "

@@ -305,6 +305,15 @@ typedef struct {
    timed launch adds two event records to its stream, so timing only the family of
    interest keeps the profiler's own cost out of the rest of the step.  ERR_ARG for a
    mask with no valid family bit. */
+/* How the eager entry points (fbsde_solve, fbsde_solve_host, fbsde_solve_noalloc,
+   fbsde_adjoint) launch the passes of a CG loop: while the profiler times the product
+   family, the first FBSDE_PROFILED_EAGER_PASSES passes of every loop are launched one by
+   one (each product launch bracketed by events; kernels of converged queries exit at
+   once) and any further passes run in a cached CUDA graph whose conditional while loop
+   stops when every query has converged.  Otherwise every pass runs in that graph.  On a
+   stream that is being captured every pass is launched one by one, up to cg_max_iter.
+   The results are the same bit for bit in every case. */
+#define FBSDE_PROFILED_EAGER_PASSES 48
 FBSDE_API int fbsde_profile_start(int32_t max_timed_launches);
 FBSDE_API int fbsde_profile_select(uint32_t family_mask);
 FBSDE_API int fbsde_profile_stop(fbsde_kernel_stats *out);

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <list>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -226,13 +227,22 @@ struct ProfScope {
     }
 };
 
+// True while the launch profiler brackets product launches with events.
+bool profiling_products()
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    return g_prof.on && ((g_prof.mask >> FBSDE_K_MATVEC) & 1u);
+}
+
 // Where the launches go: eagerly on a stream (with the optional launch profiler), or
 // into a CUDA graph being captured on that stream, with each CG loop as a conditional
-// while node whose body is captured on a second stream.
+// while node whose body is captured on a second stream.  graph_tail (eager only): the
+// CG passes that the eager loop does not launch one by one run as a cached CUDA graph.
 struct Rec {
     cudaStream_t s;
     bool capture;
     cudaStream_t body;
+    bool graph_tail;
 };
 
 #define FBSDE_TRY(fam, call)                                                                 \
@@ -241,20 +251,15 @@ struct Rec {
         if ((e = (call)) != cudaSuccess) return e;                                           \
     } while (0)
 
-// The CG iterations of one regression (all queries of the launch together).
-template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, const Rec &r)
+// The CG loop captured into the graph being built on stream s: a reset kernel that sets
+// the loop condition, then a conditional while node whose body (product, reduction, CG
+// update) is captured on the stream `body`; k_cg_update keeps the condition at 1 while
+// some query iterates and fewer than cg_max_iter passes ran.
+template <typename Real>
+cudaError_t cg_capture(const Params &p, const Layout &L, cudaStream_t s, cudaStream_t b)
 {
     using LR = Launch<Real>;
     cudaError_t e;
-    const cudaStream_t s = r.s;
-    if (!r.capture) {
-        for (int it = 0; it < p.cg_max_iter; ++it) {
-            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
-            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
-            FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_update(p, L, 0, 0, s));
-        }
-        return cudaSuccess;
-    }
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -265,7 +270,7 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
     cudaGraphConditionalHandle h;
     if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
-    if ((e = LR::cg_reset(p, s)) != cudaSuccess) return e;
+    if ((e = LR::cg_reset(p, h, s)) != cudaSuccess) return e;
     if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd)) != cudaSuccess) return e;
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
@@ -278,7 +283,6 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
                                                  cudaStreamSetCaptureDependencies)) != cudaSuccess)
         return e;
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    const cudaStream_t b = r.body;
     if ((e = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return e;
@@ -288,6 +292,119 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
     cudaGraph_t ended = nullptr;
     e = cudaStreamEndCapture(b, &ended);
     return eb != cudaSuccess ? eb : e;
+}
+
+// Cache of instantiated CG-loop graphs for the eager entry points, keyed by device,
+// precision and the bytes of the layout and of the parameters the CG kernels see (the
+// level-dependent fields are zeroed: the product, reduction and update kernels do not
+// read them, so every level of a solve shares one graph).  Least-recently used entries
+// beyond kCgCacheSize are destroyed after their last launch completes.  The cache is
+// never freed, so no CUDA call runs from a static destructor at process exit.
+constexpr size_t kCgCacheSize = 32;
+constexpr int kEagerPasses = FBSDE_PROFILED_EAGER_PASSES;
+
+struct CgGraph {
+    int dev;
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec;
+    cudaEvent_t last;
+};
+struct CgCache {
+    std::mutex mu;
+    std::list<CgGraph> lru;
+    cudaStream_t cap[64] = {}, body[64] = {};
+};
+CgCache *g_cg = new CgCache();
+
+template <typename Real> cudaError_t cg_graph_launch(const Params &p, const Layout &L, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    Params q;
+    std::memset(&q, 0, sizeof q);
+    q = p;
+    q.level = 0;
+    q.newton_level = 0;
+    q.walk = 0;
+    q.wa = q.wb = 0.0;
+    std::vector<unsigned char> key(sizeof q + sizeof L + 1);
+    std::memcpy(key.data(), &q, sizeof q);
+    std::memcpy(key.data() + sizeof q, &L, sizeof L);
+    key[sizeof q + sizeof L] = (unsigned char)sizeof(Real);
+    std::lock_guard<std::mutex> lk(g_cg->mu);
+    auto it = g_cg->lru.begin();
+    for (; it != g_cg->lru.end(); ++it)
+        if (it->dev == dev && it->key == key) break;
+    if (it == g_cg->lru.end()) {
+        if (!g_cg->cap[dev]) {
+            if ((e = cudaStreamCreateWithFlags(&g_cg->cap[dev], cudaStreamNonBlocking)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamCreateWithFlags(&g_cg->body[dev], cudaStreamNonBlocking)) != cudaSuccess)
+                return e;
+        }
+        if ((e = cudaStreamBeginCapture(g_cg->cap[dev], cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return e;
+        const cudaError_t ec = cg_capture<Real>(q, L, g_cg->cap[dev], g_cg->body[dev]);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(g_cg->cap[dev], &g);
+        if (ec != cudaSuccess || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return ec != cudaSuccess ? ec : (e != cudaSuccess ? e : cudaErrorUnknown);
+        }
+        CgGraph c{dev, key, nullptr, nullptr};
+        e = cudaGraphInstantiate(&c.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&c.last, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaGraphExecDestroy(c.exec);
+            return e;
+        }
+        g_cg->lru.push_front(c);
+        while (g_cg->lru.size() > kCgCacheSize) {
+            CgGraph &old = g_cg->lru.back();
+            cudaEventSynchronize(old.last);
+            cudaGraphExecDestroy(old.exec);
+            cudaEventDestroy(old.last);
+            g_cg->lru.pop_back();
+        }
+        it = g_cg->lru.begin();
+    } else if (it != g_cg->lru.begin()) {
+        g_cg->lru.splice(g_cg->lru.begin(), g_cg->lru, it);
+        it = g_cg->lru.begin();
+    }
+    if ((e = cudaGraphLaunch(it->exec, s)) != cudaSuccess) return e;
+    return cudaEventRecord(it->last, s);
+}
+
+// The CG iterations of one regression (all queries of the launch together).  Eager: the
+// passes are launched one by one (kernels of queries that have converged exit at once),
+// or, with graph_tail, handed to a cached CUDA graph whose conditional while loop runs
+// only the passes some query needs.  While the launch profiler times the product kernel,
+// the first kEagerPasses passes stay eager so their products can be bracketed by events.
+// A stream that is itself being captured gets the eager passes.
+template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, const Rec &r)
+{
+    using LR = Launch<Real>;
+    cudaError_t e;
+    const cudaStream_t s = r.s;
+    if (r.capture) return cg_capture<Real>(p, L, s, r.body);
+    bool tail = r.graph_tail;
+    if (tail) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if ((e = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return e;
+        tail = cs == cudaStreamCaptureStatusNone;
+    }
+    const int eager = !tail ? p.cg_max_iter
+                            : (profiling_products() ? std::min(p.cg_max_iter, kEagerPasses) : 0);
+    for (int it = 0; it < eager; ++it) {
+        FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+        FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 1, s));
+        FBSDE_TRY(FBSDE_K_CG_STEP, LR::cg_update(p, L, 0, 0, s));
+    }
+    if (eager < p.cg_max_iter) return cg_graph_launch<Real>(p, L, s);
+    return cudaSuccess;
 }
 
 // Algorithm 1: forward sweep, then the backward levels k = N-1..0.  Each level: the CG
@@ -353,7 +470,14 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
     }
     for (int k = 0; k < p.N; ++k) {
         p.level = k;
-        p.w = reinterpret_cast<Real *>(p.tape_w) + (size_t)k * L.Q * L.M;  // weights of level k
+        // weights of level k into the weight buffer (every level's kernels, and so the
+        // cached CG-loop graph, then see the same pointer)
+        {
+            const size_t wb = (size_t)L.Q * L.M * sizeof(Real);
+            if ((e = cudaMemcpyAsync(p.w, static_cast<const char *>(p.tape_w) + (size_t)k * wb, wb,
+                                     cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                return e;
+        }
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_setup(p, L, s));
         if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_post(p, L, s));
@@ -394,7 +518,7 @@ int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double
     if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
     const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, trace);
-    const Rec r{stream, false, nullptr};
+    const Rec r{stream, false, nullptr, true};
     const cudaError_t e = P->precision == FBSDE_FP32 ? run<float>(p, L, x0, theta, r)
                                                      : run<double>(p, L, x0, theta, r);
     return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
@@ -504,7 +628,7 @@ int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t 
         (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
     const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, nullptr);
-    const Rec r{reinterpret_cast<cudaStream_t>(stream), false, nullptr};
+    const Rec r{reinterpret_cast<cudaStream_t>(stream), false, nullptr, true};
     char *base = static_cast<char *>(workspace);
     const cudaError_t e =
         P->precision == FBSDE_FP32
@@ -659,7 +783,7 @@ int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, 
     for (int b = 0; b < B && e == cudaSuccess; ++b)
         e = cudaStreamWaitEvent(pl->streams[2 + b], pl->events[0], 0);
     for (int b = 0; b < B && e == cudaSuccess; ++b) {
-        const Rec r{pl->streams[2 + b], true, body};
+        const Rec r{pl->streams[2 + b], true, body, false};
         for (int i : lists[b]) {
             const PlanInstance &pi = v[i];
             void *ws = static_cast<char *>(workspace) + pi.offset;

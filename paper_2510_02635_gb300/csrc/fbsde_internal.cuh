@@ -101,7 +101,7 @@ template <typename Real> struct Launch {
     static cudaError_t cg_update(const Params &p, const Layout &L, cudaGraphConditionalHandle h,
                                int use_h, cudaStream_t s);
     static cudaError_t cg_post(const Params &p, const Layout &L, cudaStream_t s);
-    static cudaError_t cg_reset(const Params &p, cudaStream_t s);
+    static cudaError_t cg_reset(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s);
     static cudaError_t trace_forward(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, int nj, int d,
                                void *out, cudaStream_t st);

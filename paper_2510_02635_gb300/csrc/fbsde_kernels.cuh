@@ -1142,14 +1142,17 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     }
 }
 
-// Before the CUDA-graph while loop around the CG passes (its condition defaults to 1, so
-// the body runs once before k_cg_update first sets it): zero the pass counter and the
-// arrival counter, kept in the first query's state.
-template <typename Real> __global__ void k_cg_reset(Params p)
+// Before the CUDA-graph while loop around the CG passes: zero the pass counter and the
+// arrival counter (kept in the first query's state) and set the loop condition to 1 only
+// if some query still has to iterate, so a loop with nothing to do runs no pass.
+template <typename Real> __global__ void k_cg_reset(Params p, cudaGraphConditionalHandle h)
 {
     if (threadIdx.x != 0) return;
     p.st[0].loop_iter = 0;
     p.st[0].arrive = 0;
+    bool active = false;
+    for (int q = 0; q < p.Q && !active; ++q) active = p.st[q].done == 0;
+    cudaGraphSetConditional(h, active ? 1u : 0u);
 }
 
 // Trace copy of the forward-sweep end state (X_N - x0 and Y_N) into FP64 arrays.

@@ -134,9 +134,10 @@ cudaError_t Launch<Real>::cg_post(const Params &p, const Layout &L, cudaStream_t
     return cudaGetLastError();
 }
 
-template <typename Real> cudaError_t Launch<Real>::cg_reset(const Params &p, cudaStream_t s)
+template <typename Real>
+cudaError_t Launch<Real>::cg_reset(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s)
 {
-    dev::k_cg_reset<Real><<<1, 32, 0, s>>>(p);
+    dev::k_cg_reset<Real><<<1, 32, 0, s>>>(p, h);
     return cudaGetLastError();
 }
 

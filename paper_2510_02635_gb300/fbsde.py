@@ -74,6 +74,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
+FBSDE_PROFILED_EAGER_PASSES = 48   # the header constant of the same name
 
 _lock = threading.Lock()
 _lib = None

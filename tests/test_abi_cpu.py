@@ -34,6 +34,17 @@ def test_every_declared_entry_point_is_exported(lib):
     assert set(names) == set(fbsde.EXPORTS)
 
 
+def test_binding_constants_match_the_header():
+    text = open(HEADER).read()
+    for name in ("FBSDE_PROFILED_EAGER_PASSES", "FBSDE_NOALLOC_MAX_BYTES"):
+        m = re.search(r"#define\s+" + name + r"\s+\(?(\d+)u?(?:\s*<<\s*(\d+))?", text)
+        assert m, name
+        val = int(m.group(1)) << int(m.group(2) or 0)
+        assert getattr(fbsde, name) == val, name
+    m = re.search(r"FBSDE_NUM_KERNELS\s*=\s*(\d+)", text)
+    assert int(m.group(1)) == fbsde.FBSDE_NUM_KERNELS
+
+
 def test_abi_version_and_status_strings(lib):
     assert fbsde.fbsde_abi_version() == 1
     assert fbsde.fbsde_status_string(0) == "ok"
