@@ -637,7 +637,43 @@ __global__ void __launch_bounds__(256) k_moments(Params p)
         zero(acc[2][v]);
     }
     if (rg < R) {
-        for (long long j = r0 + rg; j < r1; j += R) {
+        // rows in order; the loads of kU rows are issued before their sums so that
+        // several row chunks are in flight per thread
+        constexpr int kU = 4;
+        long long j = r0 + rg;
+        for (; j + (kU - 1) * R < r1; j += kU * R) {
+            Chunk<Real> dl[kU][VM];
+            Real cw[kU][3];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const Real *cf = ws.coef(s, j + u * R);
+                cw[u][0] = cf[0];
+                cw[u][1] = cf[1];
+                cw[u][2] = cf[2];
+                const Real *drow = ws.row(s, j + u * R);
+#pragma unroll
+                for (int v = 0; v < VM; ++v) {
+                    const int c = c0 + tc + tpr * v;
+                    if (c - c0 < tile_nch) dl[u][v] = ld_chunk(drow + c * E);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+#pragma unroll
+                for (int v = 0; v < VM; ++v) {
+                    const int c = c0 + tc + tpr * v;
+                    if (c - c0 < tile_nch) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            acc[0][v].v[e] += cw[u][0] * dl[u][v].v[e];
+                            acc[1][v].v[e] += cw[u][1] * dl[u][v].v[e];
+                            acc[2][v].v[e] += cw[u][2] * dl[u][v].v[e];
+                        }
+                    }
+                }
+            }
+        }
+        for (; j < r1; j += R) {
             const Real *cf = ws.coef(s, j);
             const Real w0 = cf[0], w1 = cf[1], w2 = cf[2];
             const Real *drow = ws.row(s, j);
