@@ -421,7 +421,7 @@ def run_gpu(args, rank: int, world: int) -> None:
             "roofline": {"kernel": "matvec", "bound": "hbm", "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _matvec_traffic(w),
-                         "traffic_source": "ncu capture at Q=4, M=4096 scaled per particle-dim "
+                         "traffic_source": "ncu capture at Q=4, M=16384 scaled per particle-dim "
                                            "and per CTA (profiles/matvec_traffic.txt)",
                          "algorithmic_bytes_per_product": bytes_per_product,
                          "products_per_step": products,

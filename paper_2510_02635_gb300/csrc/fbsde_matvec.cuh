@@ -171,15 +171,23 @@ __global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matv
             const Real *buf = ring + (size_t)st * R * row_elems;
             for (int rr = team; rr < rows; rr += nteams) {
                 const Real *row = buf + (size_t)rr * row_elems;
+                // the row's weight, loaded before the dot product so that its latency is
+                // hidden behind the product and the team sum instead of following them
+                const Real wrow = wv[row0 + rr];
+                // narrow teams keep their chunks of the row in registers between the dot
+                // product and the weighted sum (one shared-memory read of the row instead
+                // of two); the 16-warp teams of the widest rows have no registers to spare
+                constexpr int kHeld = WIDE ? 1 : VPT;
+                Chunk<Real> dl[kHeld];
                 Real t = Real(0);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     const int c = tl + tthreads * v;
-                    if (c < nch) {
-                        const Chunk<Real> dl = ld_chunk(row + c * E);
+                    Chunk<Real> &x = dl[WIDE ? 0 : v];
+                    if (c < nch) x = ld_chunk(row + c * E);
+                    else zero(x);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) t += dl.v[e] * pc[v].v[e];
-                    }
+                    for (int e = 0; e < E; ++e) t += x.v[e] * pc[v].v[e];
                 }
 #pragma unroll
                 for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -191,14 +199,15 @@ __global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matv
                     for (int w2 = 0; w2 < tw; ++w2) t += sl[w2];
                     phase ^= 1;
                 }
-                const Real coef = wv[row0 + rr] * t;
+                const Real coef = wrow * t;
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     const int c = tl + tthreads * v;
                     if (c < nch) {
-                        const Chunk<Real> dl = ld_chunk(row + c * E);
+                        if (WIDE) dl[0] = ld_chunk(row + c * E);
+                        const Chunk<Real> &x = dl[WIDE ? 0 : v];
 #pragma unroll
-                        for (int e = 0; e < E; ++e) acc[v].v[e] += coef * dl.v[e];
+                        for (int e = 0; e < E; ++e) acc[v].v[e] += coef * x.v[e];
                     }
                 }
             }

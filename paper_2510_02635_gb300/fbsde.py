@@ -495,12 +495,19 @@ def _main(argv=None) -> None:
     ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--cg-max-iter", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--time-products", action="store_true",
+                    help="run the launch profiler on the product kernel (the first "
+                         "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
+                         "one by one, outside CUDA graphs, e.g. for a kernel profiler)")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
     x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)), device="cuda")
     theta = rng.uniform(0.5, 1.5, size=a.d) if a.kind in ("hjb_logquad", "affine_test") else None
     solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
                     theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
+    if a.time_products:
+        fbsde_profile_start(1 << 20)
+        fbsde_profile_select(["matvec"])
     for r in range(a.repeat):
         t0 = time.perf_counter()
         out = solver.solve(x0, seed=a.seed)
@@ -508,6 +515,10 @@ def _main(argv=None) -> None:
         dt = time.perf_counter() - t0
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
               f"u0[0]={float(out['u0'][0]):.12f}")
+    if a.time_products:
+        mv = fbsde_profile_stop()["matvec"]
+        print(f"product launches {mv['launches']}, timed {mv['timed']}, "
+              f"{mv['total_ms']:.2f} ms")
 
 
 if __name__ == "__main__":
