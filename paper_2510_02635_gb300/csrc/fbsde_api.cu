@@ -110,7 +110,7 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_Y = take(Qs * Ms * sizeof(double));
     L.off_w = take(Qs * Ms * L.real_sz);
     L.off_coef = take(Qs * Ms * 3 * L.real_sz);
-    L.off_segp = take(Qs * Ms * (size_t)L.nseg * 3 * L.real_sz);
+    L.off_segp = take(Qs * Ms * (size_t)L.nseg * kSegSums * L.real_sz);
     L.off_part = take(Qs * L.G * kPartVecs * lds * L.real_sz);
     L.off_spart = take(Qs * L.GP * kPartScal * sizeof(double));
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));

@@ -26,10 +26,11 @@ namespace fbsde {
 
 constexpr int kPartVecs = 3;
 constexpr int kPartScal = 4;
-constexpr int kVec64 = 8;
+constexpr int kVec64 = 9;
 constexpr int kRedTile = 128;  // elements per block of the partial reduction and CG update
 constexpr int kBpart = 4;      // per-block shares: w . r, S . r, r . r, spare
-constexpr int kVecR = 3;
+constexpr int kVecR = 4;
+constexpr int kSegSums = 4;   // per-row-segment sums of the row kernels
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
 constexpr int kMinRowsPerCta = 8;

@@ -340,15 +340,16 @@ template <typename Real> struct WS {
         return reinterpret_cast<Real *>(p.w) + (size_t)s * p.M;
     }
     __device__ __forceinline__ double *Y(int s) const { return p.Y + (size_t)s * p.M; }
-    // per-particle moment coefficients (w, w (Y - yref), w (D . x_ws))
+    // per-particle moment coefficients (w, w (Y - yref), w (D . g)), g the starting guess
+    // of the solve
     __device__ __forceinline__ Real *coef(int s, long long j) const
     {
         return reinterpret_cast<Real *>(p.coef) + ((size_t)s * p.M + j) * 3;
     }
-    // per-particle, per-row-segment partial sums [3]
+    // per-particle, per-row-segment partial sums [kSegSums]
     __device__ __forceinline__ Real *segp(int s, long long j, int seg) const
     {
-        return reinterpret_cast<Real *>(p.segp) + (((size_t)s * p.M + j) * p.nseg + seg) * 3;
+        return reinterpret_cast<Real *>(p.segp) + (((size_t)s * p.M + j) * p.nseg + seg) * kSegSums;
     }
     __device__ __forceinline__ Real *part(int s, int g, int v) const
     {
@@ -358,14 +359,15 @@ template <typename Real> struct WS {
     {
         return p.spart + ((size_t)s * p.GS + b) * kPartScal;
     }
-    // FP64 vectors: 0 x (= alpha_x), 1 r, 2 p, 3 S, 4 b / rhs, 5 w = A r or G, 6 x0,
-    // 7 s = A p
+    // FP64 vectors: 0 x (= alpha_x; after the level, the next level's starting guess),
+    // 1 r, 2 p, 3 S, 4 b / rhs, 5 w = A r or G, 6 x0, 7 s = A p, 8 alpha_x of the level
+    // before
     __device__ __forceinline__ double *v64(int s, int which) const
     {
         return p.vec64 + ((size_t)s * kVec64 + which) * p.ld;
     }
-    // stream-precision vectors: 0 operand of the product (r), 1 x, 2 x0; theta after all
-    // solves
+    // stream-precision vectors: 0 operand of the product (r), 1 alpha_x, 2 x0, 3 the next
+    // level's starting guess; theta after all solves
     __device__ __forceinline__ Real *vR(int s, int which) const
     {
         return reinterpret_cast<Real *>(p.vecR) + ((size_t)s * kVecR + which) * p.ld;
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(256) k_forward(Params p)
             o[0] = acc[0];
             o[1] = acc[1];
             o[2] = Real(0);
+            o[3] = Real(0);
         }
     }
 }
@@ -480,6 +483,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
         const uint32_t sidx = p.solve0 + (uint32_t)s;
         const Real *xr = ws.vR(s, 1);
         const Real *x0r = ws.vR(s, 2);
+        const Real *gr = ws.vR(s, 3);
         Real *drow = ws.row(s, j);
         Chunk<Real> dl[VPT];
 #pragma unroll
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
             const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) dl[v] = ld_chunk(drow + c * E);
         }
-        Real acc[3] = {Real(0), Real(0), Real(0)};
+        Real acc[kSegSums] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int c = seg * 32 * VPT + lane + 32 * v;
@@ -495,11 +499,13 @@ __global__ void __launch_bounds__(256) k_update(Params p)
                 const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j,
                                                    (uint32_t)k, sidx, p.key0, p.key1, p.d);
                 const Chunk<Real> xc = ldg_chunk(xr + c * E);
+                const Chunk<Real> gc = ldg_chunk(gr + c * E);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     dl[v].v[e] = wa * dl[v].v[e] + wb * z.v[e];
                     acc[0] += xc.v[e] * dl[v].v[e];
                     acc[1] += dl[v].v[e] * dl[v].v[e];
+                    acc[3] += gc.v[e] * dl[v].v[e];
                 }
                 if (cos_feature) {
                     const Chunk<Real> x0c = ldg_chunk(x0r + c * E);
@@ -516,6 +522,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
             o[0] = acc[0];
             o[1] = acc[1];
             o[2] = acc[2];
+            o[3] = acc[3];
         }
     }
 }
@@ -526,7 +533,8 @@ __global__ void __launch_bounds__(256) k_update(Params p)
 //                         coefficients (w, w (Y - g(x0)), 0);
 //   level k >= 1:         E_hat = alpha + alpha_x . Delta_k (local affine model), Newton
 //                         (2.16)-(2.17) for Y_k, w = K(|Delta_k|) for the level k-1
-//                         regression, coefficients (w, w (Y - alpha), w alpha_x . Delta_k).
+//                         regression, coefficients (w, w (Y - alpha), w g . Delta_k), g the
+//                         starting guess of that regression's solve (k_cg_post).
 // Block sums of (w, w (Y - yref), w |D|^2) go to spart in thread order.
 // ---------------------------------------------------------------------------
 template <typename Real>
@@ -544,12 +552,13 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
     double sums[3] = {0.0, 0.0, 0.0};
     int it_used = 0, failed = 0;
     if (j < p.M) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         for (int seg = 0; seg < p.nseg; ++seg) {
             const Real *sp = ws.segp(s, j, seg);
             a0 += (double)sp[0];
             a1 += (double)sp[1];
             a2 += (double)sp[2];
+            a3 += (double)sp[3];
         }
         double Yj, rho, dot = 0.0;
         if (terminal) {
@@ -581,7 +590,7 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
         Real *cf = ws.coef(s, j);
         cf[0] = wr;
         cf[1] = (Real)(wd * (Yj - yref));
-        cf[2] = (Real)(wd * dot);
+        cf[2] = (Real)(wd * a3);   // D . (starting guess of the next level's solve)
         sums[0] = wd;
         sums[1] = wd * (Yj - yref);
         sums[2] = wd * rho;
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
 
 // ---------------------------------------------------------------------------
 // Weighted moments of the next regression, a streaming column sum with three weights
-// per row: partial_g = (sum w D, sum w (Y - yref) D, sum w (D . x_ws) D) over the rows
+// per row: partial_g = (sum w D, sum w (Y - yref) D, sum w (D . g) D) over the rows
 // of CTA g.  Grid (tiles, G, Q); a tile covers 256 VM chunks of the row; threads form
 // R row groups of tpr threads (R > 1 only for narrow rows), summed in group order.
 // ---------------------------------------------------------------------------
@@ -910,6 +919,7 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
         x[i] = 0.0;
         xR[i] = Real(0);
         pR[i] = Real(0);
+        ws.vR(s, 3)[i] = Real(0);
         for (int v = 1; v < kVec64; ++v)
             if (v != 6) ws.v64(s, v)[i] = 0.0;
         if (s == 0) ws.thetaR()[i] = (Real)th;
@@ -1129,7 +1139,11 @@ __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditional
 }
 
 // After the CG solve of level k: alpha = c - S . alpha_x (Eq. 3.20), Z_k = sigma alpha_x,
-// trace outputs; at k = 0 the Newton step at x0 gives u(0,x0) (Algorithm 1).
+// trace outputs; at k = 0 the Newton step at x0 gives u(0,x0) (Algorithm 1).  The
+// starting guess of the next level's solve is the linear extrapolation in k of the last
+// two levels' alpha_x, g = 2 alpha_x^k - alpha_x^{k+1} (alpha_x^k alone at the top level):
+// it starts the CG closer to the solution than alpha_x^k does (the solutions drift
+// smoothly from level to level) and changes only the number of CG passes.
 template <typename Real>
 __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
 {
@@ -1137,12 +1151,18 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     const int s = blockIdx.x, k = p.level;
     const WS<Real> ws(p);
     SolveState &st = p.st[s];
-    const double *x = ws.v64(s, 0), *S = ws.v64(s, 3);
-    Real *xR = ws.vR(s, 1);
+    double *x = ws.v64(s, 0), *xp = ws.v64(s, 8);
+    const double *S = ws.v64(s, 3);
+    Real *xR = ws.vR(s, 1), *gR = ws.vR(s, 3);
+    const bool extrap = k + 1 < p.N;   // alpha_x of level k+1 is in slot 8
     double a[3] = {0.0, 0.0, 0.0};
     #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = x[i];
+        const double g = extrap ? 2.0 * xi - xp[i] : xi;
+        xp[i] = xi;
+        x[i] = g;
+        gR[i] = (Real)g;
         xR[i] = (Real)xi;
         a[0] += S[i] * xi;
         a[1] += xi;
