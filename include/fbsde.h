@@ -89,7 +89,8 @@ typedef enum {
 
 typedef struct {
     int32_t kind;            /* fbsde_kind                                             */
-    int32_t d;               /* dimension, 1 <= d <= FBSDE_MAX_D                       */
+    int32_t d;               /* dimension, 1 <= d <= FBSDE_MAX_D (FP64: d <= 8192,
+                                one 16-warp team per row of the product)               */
     int32_t N;               /* number of time steps, dt = T/N, N >= 1                 */
     int32_t precision;       /* fbsde_precision                                        */
     int64_t M;               /* particles per query point, M >= 2                      */
