@@ -306,8 +306,9 @@ typedef struct {
    timed launch adds two event records to its stream, so timing only the family of
    interest keeps the profiler's own cost out of the rest of the step.  ERR_ARG for a
    mask with no valid family bit. */
-/* How the eager entry points (fbsde_solve, fbsde_solve_host, fbsde_solve_noalloc,
-   fbsde_adjoint) launch the passes of a CG loop: while the profiler times the product
+/* How the eager entry points (fbsde_solve, fbsde_solve_host, fbsde_adjoint) launch the
+   passes of a CG loop (fbsde_solve_noalloc always launches every pass, up to cg_max_iter,
+   one by one on the stream, so that it creates no CUDA graph): while the profiler times the product
    family, the first FBSDE_PROFILED_EAGER_PASSES passes of every loop are launched one by
    one (each product launch bracketed by events; kernels of converged queries exit at
    once) and any further passes run in a cached CUDA graph whose conditional while loop

@@ -505,7 +505,7 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
 int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double *theta,
                uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
                const fbsde_trace *trace, void *workspace, size_t workspace_bytes,
-               cudaStream_t stream)
+               cudaStream_t stream, bool graph_tail = true)
 {
     Layout L;
     int st = check_problem(P, Q, false);
@@ -518,7 +518,7 @@ int solve_impl(const fbsde_problem *P, int32_t Q, const double *x0, const double
     if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
         return FBSDE_ERR_WORKSPACE;
     const Params p = make_params(P, L, workspace, seed, solve_index0, u0, grad_u0, trace);
-    const Rec r{stream, false, nullptr, true};
+    const Rec r{stream, false, nullptr, graph_tail};
     const cudaError_t e = P->precision == FBSDE_FP32 ? run<float>(p, L, x0, theta, r)
                                                      : run<double>(p, L, x0, theta, r);
     return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
@@ -566,6 +566,18 @@ __global__ void k_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out
 }
 
 }  // namespace
+}  // namespace fbsde
+
+namespace fbsde {
+// fbsde_solve with every CG pass launched on the stream (no CUDA graph is created,
+// instantiated or cached), for the entry point that must allocate nothing.
+int solve_launches_only(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                        uint32_t solve_index0, double *u0, double *grad_u0, void *workspace,
+                        size_t workspace_bytes, cudaStream_t stream)
+{
+    return solve_impl(P, Q, x0, P ? P->theta : nullptr, seed, solve_index0, u0, grad_u0,
+                      nullptr, workspace, workspace_bytes, stream, false);
+}
 }  // namespace fbsde
 
 using namespace fbsde;

@@ -24,6 +24,12 @@
 
 namespace fbsde {
 
+// fbsde_solve with every CG pass launched on the stream, creating no CUDA graph
+// (fbsde_api.cu); used by the entry point without a workspace argument.
+int solve_launches_only(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                        uint32_t solve_index0, double *u0, double *grad_u0, void *workspace,
+                        size_t workspace_bytes, cudaStream_t stream);
+
 constexpr int kPartVecs = 3;
 constexpr int kPartScal = 4;
 constexpr int kVec64 = 9;

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "../../include/fbsde.h"
+#include "fbsde_internal.cuh"
 
 namespace {
 
@@ -48,6 +49,9 @@ extern "C" int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const doub
     void *scratch = nullptr;
     const int st = scratch_address(&scratch);
     if (st != FBSDE_OK) return st;
-    return fbsde_solve(P, Q, x0, seed, solve_index0, u0, grad_u0, nullptr, scratch,
-                       (size_t)FBSDE_NOALLOC_MAX_BYTES, stream);
+    // every CG pass is launched on the stream: the cached CUDA graphs of fbsde_solve would
+    // create streams and instantiate graphs, which may allocate
+    return fbsde::solve_launches_only(P, Q, x0, seed, solve_index0, u0, grad_u0, scratch,
+                                      (size_t)FBSDE_NOALLOC_MAX_BYTES,
+                                      reinterpret_cast<cudaStream_t>(stream));
 }
