@@ -47,6 +47,7 @@ typedef struct CUstream_st *fbsde_stream_t; /* the same handle as cudaStream_t *
 
 #define FBSDE_ABI_VERSION 1
 #define FBSDE_MAX_D 16384 /* largest dimension d accepted */
+#define FBSDE_MAX_D_FP64 8192 /* largest d of the FP64 path (one 16-warp team per row) */
 
 typedef enum {
     FBSDE_OK = 0,
@@ -89,8 +90,8 @@ typedef enum {
 
 typedef struct {
     int32_t kind;            /* fbsde_kind                                             */
-    int32_t d;               /* dimension, 1 <= d <= FBSDE_MAX_D (FP64: d <= 8192,
-                                one 16-warp team per row of the product)               */
+    int32_t d;               /* dimension, 1 <= d <= FBSDE_MAX_D (FBSDE_MAX_D_FP64 on
+                                the FP64 path)                                         */
     int32_t N;               /* number of time steps, dt = T/N, N >= 1                 */
     int32_t precision;       /* fbsde_precision                                        */
     int64_t M;               /* particles per query point, M >= 2                      */

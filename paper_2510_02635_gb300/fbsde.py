@@ -74,6 +74,8 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
+FBSDE_MAX_D = 16384
+FBSDE_MAX_D_FP64 = 8192
 FBSDE_PROFILED_EAGER_PASSES = 48   # the header constant of the same name
 
 _lock = threading.Lock()

@@ -36,7 +36,8 @@ def test_every_declared_entry_point_is_exported(lib):
 
 def test_binding_constants_match_the_header():
     text = open(HEADER).read()
-    for name in ("FBSDE_PROFILED_EAGER_PASSES", "FBSDE_NOALLOC_MAX_BYTES"):
+    for name in ("FBSDE_PROFILED_EAGER_PASSES", "FBSDE_NOALLOC_MAX_BYTES", "FBSDE_MAX_D",
+                 "FBSDE_MAX_D_FP64"):
         m = re.search(r"#define\s+" + name + r"\s+\(?(\d+)u?(?:\s*<<\s*(\d+))?", text)
         assert m, name
         val = int(m.group(1)) << int(m.group(2) or 0)

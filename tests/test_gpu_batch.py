@@ -25,7 +25,7 @@ def _sample(instances):
 
 def test_batched_plan_matches_oracle_on_sampled_instances():
     from paper_2510_02635_gb300 import autotune
-    inst = W.batch_instances()
+    inst = autotune.route_precision(W.batch_instances())
     x0s = W.batch_x0(inst)
     table = autotune.tune(inst)
     batch = autotune.Batch(inst, x0s, table)
@@ -58,3 +58,28 @@ def test_per_instance_fp64_form_matches_oracle():
     ru, rg = rel_errors(float(plan.u0[0][0]), plan.grad[0][0].cpu().numpy(), ref)
     assert ru <= TOL_FP64 and rg <= TOL_FP64
     plan.close()
+
+
+def test_routed_batch_has_the_accuracy_of_the_fp64_form():
+    """The first 32 batch instances, precision routed by conditioning (FP32 where the
+    regression's estimated condition number allows it), against each instance solved
+    alone in FP64: u and grad u within 1e-4 relative for every instance."""
+    from paper_2510_02635_gb300 import autotune, fbsde
+    inst = autotune.route_precision(W.batch_instances())[:32]
+    assert any(w.precision == "fp64" for w in inst) and any(w.precision == "fp32" for w in inst)
+    x0s = W.batch_x0(W.batch_instances())[:32]
+    batch = autotune.Batch(inst, x0s, None)
+    batch.launch()
+    torch.cuda.synchronize()
+    u32, g32 = batch.results()
+    batch.close()
+    for i, w in enumerate(W.batch_instances(precision="fp64")[:32]):
+        plan = fbsde.Plan([{"problem": autotune.problem_of(w), "Q": 1, "seed": w.seed,
+                            "x0": torch.tensor(x0s[i], device="cuda"), "solve_index0": i}])
+        plan.launch()
+        torch.cuda.synchronize()
+        u64, g64 = float(plan.u0[0][0]), plan.grad[0][0].cpu().numpy()
+        plan.close()
+        scale = max(np.linalg.norm(g64), abs(u64))
+        assert abs(u32[i] - u64) <= TOL_FP32 * abs(u64), (i, w.d, w.M)
+        assert np.linalg.norm(g32[i] - g64) <= TOL_FP32 * scale, (i, w.d, w.M)
