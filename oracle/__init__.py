@@ -99,6 +99,9 @@ def _load():
                                       C.c_int32, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp,
                                       _dp]
             lib.orc_solve.restype = C.c_int
+            lib.orc_solve_anchored.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64,
+                                               C.c_uint32, _dp, _dp]
+            lib.orc_solve_anchored.restype = C.c_int
             lib.orc_adjoint.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, _dp,
                                         _dp, _dp]
             lib.orc_adjoint.restype = C.c_int
@@ -277,6 +280,19 @@ def solve(prob: Problem, x0, seed: int, solve_index: int = 0, max_levels: int | 
     if keep_levels_y:
         out.update(Y_levels=y_lv)
     return out
+
+
+def solve_anchored(prob: Problem, x0, seed: int, solve_index: int = 0) -> dict:
+    """Algorithm 1 with one regression per particle anchor (each particle's own position
+    at level k).  Returns u0, grad (alpha_x of level 0) and status."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    assert x0.shape == (prob.d,)
+    u0 = C.c_double(math.nan)
+    grad = np.zeros(prob.d)
+    ps = prob.c_struct()
+    st = _load().orc_solve_anchored(C.byref(ps), _ptr(x0), int(seed), int(solve_index),
+                                    C.byref(u0), _ptr(grad))
+    return {"u0": float(u0.value), "grad": grad, "status": int(st)}
 
 
 def g_grad(prob: Problem, x) -> tuple[np.ndarray, np.ndarray]:

@@ -616,6 +616,91 @@ int orc_solve(const orc_problem *P, const double *x0, uint64_t seed, uint32_t so
     return status;
 }
 
+/*
+ * Algorithm 1 in its literal form: one regression per particle anchor.  At level k the
+ * anchor of particle m is its own position X_k^m (Algorithm 1's backward loop over m;
+ * the local linear approximation (2.9) centred at X_k^m), and
+ *   D_j^m = X_{k+1}^j - X_k^m   (next-level positions minus the anchor, as in R2),
+ *   Gaussian weights (2.11), Remark 2.3, with eps_k^2 = h^2 E|D^m|^2,
+ *     E|D^m|^2 = sigma^2 d (t_k + t_{k+1})   (two independent paths from x0),
+ *   the ridge regression of Y_{k+1}^j on D^m (Eqs. 3.19-3.20, Remark 2.2) -> alpha^m,
+ *   alpha_x^m; Z_k^m = sigma alpha_x^m; the local model at the anchor, E_hat_m = alpha^m;
+ *   Newton (2.16)-(2.17): Y_k^m = alpha^m + dt f(t_k, X_k^m, Y_k^m, Z_k^m).
+ * u(0,x0) = (1/M) sum_m Y_0^m; at k = 0 every anchor is x0, so every regression is the
+ * same and grad u(0,x0) = alpha_x^1 of level 0.  With uniform weights (h = inf) the
+ * regressions differ only by a shift of D, which leaves alpha_x unchanged and moves
+ * alpha^m to alpha + alpha_x . (X_k^m - x0): the result is orc_solve's.
+ * The particle paths are those of orc_solve (path_end, path_step).  Cost O(M^2 d) per
+ * level (M regressions over M particles).  Outputs u0, grad_u0[d] (may be NULL).
+ */
+int orc_solve_anchored(const orc_problem *P, const double *x0, uint64_t seed,
+                       uint32_t solve_index, double *u0, double *grad_u0)
+{
+    const int d = P->d, N = P->N;
+    const int64_t M = P->M;
+    if (d < 1 || N < 1 || M < 2 || !(P->T > 0.0) || !(P->sigma > 0.0)) return ORC_ERR_ARG;
+    if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta)
+        return ORC_ERR_ARG;
+    const double dt = P->T / N;
+    const size_t Md = (size_t)M * (size_t)d;
+    double *Xn = (double *)malloc(sizeof(double) * Md);   /* X_{k+1} */
+    double *Xk = (double *)malloc(sizeof(double) * Md);   /* X_k (the anchors) */
+    double *D = (double *)malloc(sizeof(double) * Md);
+    double *Y = (double *)malloc(sizeof(double) * M);
+    double *Yk = (double *)malloc(sizeof(double) * M);
+    double *ax = (double *)malloc(sizeof(double) * d);
+    double *z = (double *)malloc(sizeof(double) * d);
+    double *xi = (double *)malloc(sizeof(double) * d);
+    int status = ORC_OK;
+    if (!Xn || !Xk || !D || !Y || !Yk || !ax || !z || !xi) {
+        status = ORC_ERR_NOMEM;
+        goto done;
+    }
+    for (int64_t j = 0; j < M; ++j) {
+        path_end(P, x0, seed, solve_index, j, Xn + j * (int64_t)d, xi);
+        Y[j] = orc_g(P, Xn + j * (int64_t)d);   /* terminal condition, Algorithm 1 */
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        const double t_k = k * dt;
+        for (int64_t j = 0; j < M; ++j)
+            path_step(P, k, x0, seed, solve_index, j, Xn + j * (int64_t)d, Xk + j * (int64_t)d, xi);
+        const double rho_ref = P->sigma * P->sigma * d * (t_k + (k + 1) * dt);
+        for (int64_t m = 0; m < M; ++m) {
+            const double *a = Xk + m * (int64_t)d;
+            for (int64_t j = 0; j < M; ++j)
+                for (int i = 0; i < d; ++i) D[j * (int64_t)d + i] = Xn[j * (int64_t)d + i] - a[i];
+            double alpha;
+            int cg_it = 0;
+            const int st = orc_llr(d, M, D, Y, rho_ref, P->h, P->ridge_rel, P->cg_tol,
+                                   P->cg_max_iter, &alpha, ax, NULL, &cg_it);
+            if (st == ORC_ERR_NOMEM || st == ORC_ERR_ARG) {
+                status = st;
+                goto done;
+            }
+            if (st != ORC_OK && status == ORC_OK) status = st;
+            for (int i = 0; i < d; ++i) z[i] = P->sigma * ax[i];   /* Z_k^m = sigma alpha_x^m */
+            const double feat = orc_f_feature(P, t_k, a, z);
+            int it;
+            Yk[m] = orc_newton(P, alpha, dt, feat, &it);
+            if (it < 0 && status == ORC_OK) status = ORC_ERR_NEWTON;
+            if (k == 0 && m == 0 && grad_u0) memcpy(grad_u0, ax, sizeof(double) * d);
+        }
+        memcpy(Y, Yk, sizeof(double) * M);
+        double *tmp = Xn;   /* level k's positions are the cloud of level k-1 */
+        Xn = Xk;
+        Xk = tmp;
+    }
+    {
+        double s = 0.0;
+        for (int64_t m = 0; m < M; ++m) s += Y[m];
+        if (u0) *u0 = s / M;   /* Y_0 = (1/M) sum_m Y_0^m, Algorithm 1 */
+        if (!isfinite(s / M) && status == ORC_OK) status = ORC_ERR_NONFINITE;
+    }
+done:
+    free(Xn); free(Xk); free(D); free(Y); free(Yk); free(ax); free(z); free(xi);
+    return status;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Derivatives of the problem table used by the adjoint.                      */
 /* ------------------------------------------------------------------------- */
