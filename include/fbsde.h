@@ -191,6 +191,28 @@ FBSDE_API int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const doubl
                                   uint64_t seed, uint32_t solve_index0, double *u0,
                                   double *grad_u0, fbsde_stream_t stream);
 
+/*
+ * Algorithm 1 in its literal form: one regression per particle anchor.  At level k the
+ * anchor of particle m is its own position X_k^m (Algorithm 1's backward loop over m, the
+ * local linear approximation (2.9) centred at X_k^m): D_j^m = X_{k+1}^j - X_k^m, Gaussian
+ * weights (2.11) with eps_k^2 = h^2 sigma^2 d (t_k + t_{k+1}), the ridge regression of
+ * Lemma 3.7 / Remark 2.2 per anchor, Z_k^m = sigma alpha_x^m, and Newton (2.16)-(2.17)
+ * with the anchor's own intercept alpha^m and Z_k^m.  u(0,x0) = mean_m Y_0^m; grad_u0 is
+ * alpha_x at k = 0 (all anchors are x0 there).  Cost O(M^2 d) per level and CG pass: the
+ * M regressions share two M x M x d contractions per pass.  With uniform weights
+ * (h <= 0 or inf) the result equals fbsde_solve's up to rounding.
+ *   Same arguments as fbsde_solve (no trace); M <= 32768; theta (if the kind needs it)
+ *   is a device pointer in P->theta; workspace >= fbsde_anchored_workspace_bytes(P)
+ *   bytes, 256-byte aligned, reused for the Q queries one after the other.
+ * The call blocks the host: it reads the count of anchors still iterating every four CG
+ * passes.  Returns FBSDE_OK, an argument error, or the first device status (FBSDE_ERR_CG,
+ * FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE).
+ */
+FBSDE_API size_t fbsde_anchored_workspace_bytes(const fbsde_problem *P);
+FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
+                                   uint32_t solve_index0, double *u0, double *grad_u0,
+                                   void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
 /* Bytes of device workspace that fbsde_adjoint needs (the solve's workspace plus a tape
    of N (M + 2 d) values per query).  0 when the arguments are invalid. */
 FBSDE_API size_t fbsde_adjoint_workspace_bytes(const fbsde_problem *P, int32_t Q);

@@ -71,7 +71,8 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_profile_start", "fbsde_profile_select", "fbsde_profile_stop", "fbsde_kernel_name",
            "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
-           "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics"]
+           "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
+           "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
 FBSDE_MAX_D = 16384
@@ -120,6 +121,10 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_kernel_name.restype = C.c_char_p
         lib.fbsde_solve_noalloc.argtypes = [P, I32, V, U64, U32, V, V, V]
         lib.fbsde_solve_noalloc.restype = C.c_int
+        lib.fbsde_anchored_workspace_bytes.argtypes = [P]
+        lib.fbsde_anchored_workspace_bytes.restype = SZ
+        lib.fbsde_solve_anchored.argtypes = [P, I32, V, U64, U32, V, V, V, SZ, V]
+        lib.fbsde_solve_anchored.restype = C.c_int
         lib.fbsde_adjoint_workspace_bytes.argtypes = [P, I32]
         lib.fbsde_adjoint_workspace_bytes.restype = SZ
         lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
@@ -211,6 +216,35 @@ def fbsde_solve_noalloc(problem: fbsde_problem, Q: int, x0, seed: int, solve_ind
     return int(load_library().fbsde_solve_noalloc(
         C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
         _ptr(grad_u0), _stream(stream)))
+
+
+def fbsde_anchored_workspace_bytes(problem: fbsde_problem) -> int:
+    return int(load_library().fbsde_anchored_workspace_bytes(C.byref(problem)))
+
+
+def fbsde_solve_anchored(problem: fbsde_problem, Q: int, x0, seed: int, solve_index0: int,
+                         u0, grad_u0, workspace, stream=None) -> int:
+    """Algorithm 1 with one regression per particle anchor (blocking call)."""
+    return int(load_library().fbsde_solve_anchored(
+        C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream)))
+
+
+def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0) -> dict:
+    """Per-anchor solve of the CUDA tensor x0 [Q, d]; returns u0 [Q], grad [Q, d], status."""
+    import torch
+    Q = x0.shape[0]
+    nbytes = fbsde_anchored_workspace_bytes(problem)
+    if nbytes == 0:
+        raise ValueError("invalid problem for the per-anchor solve")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=x0.device)
+    u = torch.empty(Q, dtype=torch.float64, device=x0.device)
+    g = torch.empty(Q, problem.d, dtype=torch.float64, device=x0.device)
+    st = fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws)
+    if st not in (FBSDE_OK, FBSDE_ERR_CG, FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE):
+        check(st, "fbsde_solve_anchored")
+    return {"u0": u, "grad": g, "status": st}
 
 
 def fbsde_adjoint_workspace_bytes(problem: fbsde_problem, Q: int) -> int:

@@ -1,0 +1,98 @@
+"""Algorithm 1 with one regression per particle anchor: the CUDA path against the oracle's
+literal per-anchor solve on the same seeds (FP64 within 1e-10, FP32 within 1e-4), and, with
+uniform weights, against the single-anchor entry point.  Sizes are ragged with respect to
+the 64 x 64 tiles of the contractions and the 16-byte row chunks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TOL_FP32, TOL_FP64
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("ac_manufactured", 10, 150, 4, {}),
+    ("ac_manufactured", 37, 200, 3, {"h": 1.0}),
+    ("logistic_grad", 12, 97, 3, {"sigma": 12.0, "T": 1.0}),
+    ("hjb_logquad", 9, 130, 3, {"sigma": math.sqrt(2.0), "T": 1.0, "theta": True}),
+    ("ac_doublewell", 16, 65, 4, {"sigma": math.sqrt(2.0), "T": 0.3}),
+    ("cos_linear_test", 5, 64, 3, {"c1": 0.4}),
+]
+
+
+def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13):
+    extra = dict(extra)
+    sigma, T, h = extra.pop("sigma", 1.0), extra.pop("T", 0.5), extra.pop("h", 2.0)
+    rng = np.random.default_rng(d * 1000 + M)
+    theta = rng.uniform(0.5, 1.5, d) if extra.pop("theta", False) else None
+    x0 = rng.normal(scale=0.4, size=(Q, d))
+    tol = 1e-13 if prec == "fp64" else 1e-7
+    th_dev = torch.tensor(theta, device="cuda") if theta is not None else None
+    p = fb.make_problem(kind, d, N, M, sigma, T, prec, theta=th_dev, h=h, cg_tol=tol,
+                        cg_max_iter=1000, **extra)
+    out = fb.solve_anchored(p, torch.tensor(x0, device="cuda"), seed, 0)
+    torch.cuda.synchronize()
+    op = oracle.Problem(kind, d, sigma, T, N, M, theta=theta, h=h, cg_tol=1e-13,
+                        cg_max_iter=1000, **extra)
+    refs = [oracle.solve_anchored(op, x0[q], seed, q) for q in range(Q)]
+    return out, refs, p, x0, th_dev
+
+
+def _check(out, refs, tol):
+    assert out["status"] == 0
+    for q, ref in enumerate(refs):
+        assert ref["status"] == 0
+        u, g = float(out["u0"][q]), out["grad"][q].cpu().numpy()
+        assert abs(u - ref["u0"]) <= tol * abs(ref["u0"]), (q, u, ref["u0"])
+        scale = max(np.linalg.norm(ref["grad"]), abs(ref["u0"]))
+        assert np.linalg.norm(g - ref["grad"]) <= tol * scale, q
+
+
+@pytest.mark.parametrize("kind,d,M,N,extra", CASES)
+def test_fp64_matches_oracle(kind, d, M, N, extra):
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, kind, d, M, N, "fp64", extra)
+    _check(out, refs, TOL_FP64)
+
+
+@pytest.mark.parametrize("kind,d,M,N,extra", CASES)
+def test_fp32_matches_oracle(kind, d, M, N, extra):
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, kind, d, M, N, "fp32", extra)
+    _check(out, refs, TOL_FP32)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32", TOL_FP32)])
+def test_uniform_weights_equal_the_single_anchor_solve(prec, tol):
+    """h = inf: every anchor's fit is the single-anchor fit shifted, so u and grad u are
+    the single-anchor entry point's."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    d, M, N, Q = 20, 180, 4, 2
+    x0 = torch.tensor(np.random.default_rng(3).normal(scale=0.4, size=(Q, d)), device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, prec, h=math.inf,
+                        cg_tol=1e-13 if prec == "fp64" else 1e-7, cg_max_iter=1000)
+    a = fb.solve_anchored(p, x0, 21, 0)
+    ws = torch.empty(fb.fbsde_workspace_bytes(p, Q), dtype=torch.uint8, device="cuda")
+    u = torch.empty(Q, dtype=torch.float64, device="cuda")
+    g = torch.empty(Q, d, dtype=torch.float64, device="cuda")
+    fb.check(fb.fbsde_solve(p, Q, x0, 21, 0, u, g, ws))
+    torch.cuda.synchronize()
+    assert a["status"] == 0
+    assert torch.all(torch.abs(a["u0"] - u) <= tol * torch.abs(u))
+    scale = torch.maximum(torch.linalg.norm(g, dim=1), torch.abs(u))
+    assert torch.all(torch.linalg.norm(a["grad"] - g, dim=1) <= tol * scale)
+
+
+def test_argument_errors():
+    from paper_2510_02635_gb300 import fbsde as fb
+    fb.load_library()
+    assert fb.fbsde_anchored_workspace_bytes(
+        fb.make_problem("ac_manufactured", 10, 3, 40000, 1.0, 0.5, "fp32")) == 0   # M > 32768
+    p = fb.make_problem("hjb_logquad", 10, 3, 64, 1.0, 0.5, "fp32")   # theta missing
+    ws = torch.empty(fb.fbsde_anchored_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    x0 = torch.zeros(1, 10, dtype=torch.float64, device="cuda")
+    u = torch.empty(1, dtype=torch.float64, device="cuda")
+    assert fb.fbsde_solve_anchored(p, 1, x0, 0, 0, u, None, ws) == fb.FBSDE_ERR_ARG
