@@ -276,6 +276,37 @@ def extra_adjoint() -> dict:
             "note": "adjoint = re-run of the solve with its tape + the reverse sweep"}
 
 
+def extra_anchored() -> dict:
+    """Algorithm 1 with one regression per particle anchor on the plain-scheme workload
+    (Allen-Cahn with manufactured source, d = 100, M = 2048, N = 10, x0 = 0, FP32), against
+    the single-anchor solve and the closed form u*(0, x0) = e^{-T} mean_i cos x0_i."""
+    import torch
+
+    from paper_2510_02635_gb300 import fbsde
+    w = W.C0_AC_D100.with_(precision="fp32", cg_tol=1e-6)
+    x0 = torch.zeros(1, w.d, dtype=torch.float64, device="cuda")
+    p = fbsde.make_problem(w.kind, w.d, w.N, w.M, w.sigma, w.T, w.precision, h=w.h,
+                           ridge_rel=w.ridge_rel, cg_tol=w.cg_tol)
+    ws = torch.empty(fbsde.fbsde_anchored_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    u = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(1, w.d, dtype=torch.float64, device="cuda")
+
+    def run():
+        fbsde.fbsde_solve_anchored(p, 1, x0, w.seed, 0, u, g, ws)
+
+    ms = _events_ms(run, 3)
+    u_anchored = float(u[0])
+    single = fbsde.Solver(w.kind, w.d, w.N, w.M, w.sigma, w.T, Q=1, precision=w.precision,
+                          h=w.h, ridge_rel=w.ridge_rel, cg_tol=w.cg_tol)
+    u_single = float(single.solve(x0, seed=w.seed)["u0"][0])
+    exact = math.exp(-w.T) * 1.0   # mean of cos 0
+    return {"workload": "ac_manufactured_d100_M2048_N10_Q1_fp32_per_anchor", "ms_per_solve": ms,
+            "unit_note": "M^2 d N anchor-particle-dims per solve",
+            "value": w.M * w.M * w.d * w.N / (ms * 1e-3),
+            "u0": u_anchored, "u0_single_anchor": u_single, "u0_exact": exact,
+            "abs_err": abs(u_anchored - exact), "abs_err_single_anchor": abs(u_single - exact)}
+
+
 def extra_logistic() -> dict:
     """The d = 1000, 64-query logistic workload through a plan (device-side CG loops)."""
     import torch
@@ -422,7 +453,7 @@ def run_gpu(args, rank: int, world: int) -> None:
         del ws
         torch.cuda.empty_cache()
         extras = {"batched": extra_batched(), "adjoint": extra_adjoint(),
-                  "logistic_d1000_plan": extra_logistic()}
+                  "logistic_d1000_plan": extra_logistic(), "per_anchor": extra_anchored()}
 
     if rank == 0:
         line = {

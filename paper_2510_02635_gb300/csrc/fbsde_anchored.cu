@@ -41,10 +41,13 @@ struct Anchor {
 //   TN = false: C[r][c] = sum_k A[r][k] B[c][k]   (A: Mr x K, B: Nc x K, row-major)
 //   TN = true:  C[r][c] = sum_k A[k][r] B[k][c]   (A: K x Mr, B: K x Nc, row-major)
 // The sum over k runs in tile order and, inside a tile, in k order (fixed per layout).
+// Split K: block z sums k in [z kc, (z+1) kc) into its own output C + z Mr ldc; the
+// consumers add the splits in z order.
 // ---------------------------------------------------------------------------
 template <typename Real, bool TN>
-__global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, const Real *__restrict__ A,
-                                              int lda, const Real *__restrict__ B, int ldb,
+__global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, int kc,
+                                              const Real *__restrict__ A, int lda,
+                                              const Real *__restrict__ B, int ldb,
                                               Real *__restrict__ C, int ldc)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
@@ -52,19 +55,21 @@ __global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, const Real 
     __shared__ Real Bs[BK][BN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    C += (size_t)blockIdx.z * Mr * ldc;
     Real acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = Real(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kb; k0 < ke; k0 += BK) {
         for (int e = threadIdx.x; e < BM * BK; e += 256) {
             int kk, rr;
             if (TN) { kk = e / BM; rr = e - kk * BM; }
             else { rr = e / BK; kk = e - rr * BK; }
             const int gr = r0 + rr, gk = k0 + kk;
             Real v = Real(0);
-            if (gr < Mr && gk < K) v = TN ? A[(size_t)gk * lda + gr] : A[(size_t)gr * lda + gk];
+            if (gr < Mr && gk < ke) v = TN ? A[(size_t)gk * lda + gr] : A[(size_t)gr * lda + gk];
             As[kk][rr] = v;
         }
         for (int e = threadIdx.x; e < BN * BK; e += 256) {
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, const Real 
             else { cc = e / BK; kk = e - cc * BK; }
             const int gc = c0 + cc, gk = k0 + kk;
             Real v = Real(0);
-            if (gc < Nc && gk < K) v = TN ? B[(size_t)gk * ldb + gc] : B[(size_t)gc * ldb + gk];
+            if (gc < Nc && gk < ke) v = TN ? B[(size_t)gk * ldb + gc] : B[(size_t)gc * ldb + gk];
             Bs[kk][cc] = v;
         }
         __syncthreads();
@@ -201,63 +206,91 @@ __global__ void __launch_bounds__(128) k_anc_rows(Params p, const Real *P, const
     }
 }
 
-// Column pass over j for every anchor m (thread per anchor, rows in order):
-//   mode 0: w_jm from rho_jm = pn_j + an_m - 2 G_jm, stored in W; W_m, sum w Y, sum w rho.
-//   mode 1: T_jm = w_jm (G_jm - A_m . v_m) / W_m stored in T; sum_j T_jm.
+// Column pass over the rows j of chunk blockIdx.y (kRowChunk rows, in order) for every
+// anchor m (thread per anchor); per-chunk partial sums go to part[chunk][m][.] and the
+// consumers add the chunks in order.
+//   mode 0: w_jm from rho_jm = pn_j + an_m - 2 G_jm, stored in W; sums w, w Y, w rho.
+//   mode 1: T_jm = w_jm (G_jm - A_m . v_m) / W_m stored in T; sum T.
+constexpr int kRowChunk = 64;
 template <typename Real>
 __global__ void k_anc_columns(Params p, int mode, double rho_ref, const Real *G, const double *pn,
-                              const double *an, const double *Y, Real *W, Real *T, Anchor *st,
-                              double *colsum)
+                              const double *an, const double *Y, Real *W, Real *T,
+                              const Anchor *st, double *part)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
-    Anchor &a = st[m];
+    const long long j0 = (long long)blockIdx.y * kRowChunk;
+    const long long j1 = min((long long)p.M, j0 + kRowChunk);
+    double *o = part + ((size_t)blockIdx.y * p.M + m) * 3;
+    // arithmetic in the stream precision (the FP64 pipe is a small fraction of the FP32
+    // one on this part); the chunk sums are widened to FP64
     if (mode == 0) {
-        double sw = 0.0, swy = 0.0, swr = 0.0;
-        const double am = an[m];
-        for (long long j = 0; j < p.M; ++j) {
-            const double rho = fmax(pn[j] + am - 2.0 * (double)G[(size_t)j * p.M + m], 0.0);
-            const double w = dev::kernel_weight(p, rho, rho_ref);
-            W[(size_t)j * p.M + m] = (Real)w;
-            const double wr = (double)(Real)w;
-            sw += wr;
-            swy += wr * Y[j];
-            swr += wr * rho;
+        Real sw = 0, swy = 0, swr = 0;
+        const Real am = (Real)an[m], ref = (Real)rho_ref;
+        const Real scale = p.uniform ? Real(0) : (Real)(-1.0 / (p.h2 * rho_ref));
+        for (long long j = j0; j < j1; ++j) {
+            const Real rho = max((Real)pn[j] + am - Real(2) * G[(size_t)j * p.M + m], Real(0));
+            const Real w = exp((rho - ref) * scale);
+            W[(size_t)j * p.M + m] = w;
+            sw += w;
+            swy += w * (Real)Y[j];
+            swr += w * rho;
         }
-        a.W = sw;
-        a.c = swy / sw;
-        colsum[m] = swr / sw;
+        o[0] = (double)sw;
+        o[1] = (double)swy;
+        o[2] = (double)swr;
     } else {
+        const Anchor &a = st[m];
         if (a.done) return;
-        const double inv = 1.0 / a.W, ap = a.ap;
-        double s = 0.0;
-        for (long long j = 0; j < p.M; ++j) {
+        const Real inv = (Real)(1.0 / a.W), ap = (Real)a.ap;
+        Real sum = 0;
+        for (long long j = j0; j < j1; ++j) {
             const size_t ix = (size_t)j * p.M + m;
-            const Real t = (Real)((double)W[ix] * ((double)G[ix] - ap) * inv);
+            const Real t = W[ix] * (G[ix] - ap) * inv;
             T[ix] = t;
-            s += (double)t;
+            sum += t;
         }
-        colsum[m] = s;
+        o[0] = (double)sum;
     }
 }
 
 // Per anchor (one block): S, rhs, lambda, and the CG start x = 0, r = p = rhs.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_anc_setup(Params p, const Real *A, const Real *G2,
-                                                   const Real *G3, const double *colsum,
-                                                   Anchor *st, double *S, double *rhs, double *x,
-                                                   double *r, double *pv, Real *V)
+__global__ void __launch_bounds__(256) k_anc_setup(Params p, int nrc, int nsplit, const Real *A,
+                                                   const Real *G2, const Real *G3,
+                                                   const double *part, Anchor *st, double *S,
+                                                   double *rhs, double *x, double *r, double *pv,
+                                                   Real *V)
 {
     __shared__ double sm[32 * 4];
+    __shared__ double sw_sh[3];
     const int m = blockIdx.x;
     Anchor &a = st[m];
-    const double invW = 1.0 / a.W, c = a.c;
-    const size_t o = (size_t)m * p.ld;
+    if (threadIdx.x == 0) {   // the column sums of the weights, chunks in order
+        double sw = 0.0, swy = 0.0, swr = 0.0;
+        for (int c = 0; c < nrc; ++c) {
+            const double *o = part + ((size_t)c * p.M + m) * 3;
+            sw += o[0];
+            swy += o[1];
+            swr += o[2];
+        }
+        sw_sh[0] = sw;
+        sw_sh[1] = swy / sw;
+        sw_sh[2] = swr / sw;
+    }
+    __syncthreads();
+    const double invW = 1.0 / sw_sh[0], c = sw_sh[1];
+    const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // |S|^2, |rhs|^2, S . rhs, A . rhs
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        const double g2 = (double)G2[o + i] * invW;
+        double g2 = 0.0, g3 = 0.0;
+        for (int z = 0; z < nsplit; ++z) {
+            g2 += (double)G2[z * split + o + i];
+            g3 += (double)G3[z * split + o + i];
+        }
+        g2 *= invW;
         const double s = g2 - (double)A[o + i];
-        const double b = (double)G3[o + i] * invW - c * g2;
+        const double b = g3 * invW - c * g2;
         S[o + i] = s;
         rhs[o + i] = b;
         x[o + i] = 0.0;
@@ -271,7 +304,9 @@ __global__ void __launch_bounds__(256) k_anc_setup(Params p, const Real *A, cons
     }
     bsum(acc, sm);
     if (threadIdx.x == 0) {
-        a.lam = p.ridge_rel * (colsum[m] - acc[0]) / p.d;
+        a.W = sw_sh[0];
+        a.c = c;
+        a.lam = p.ridge_rel * (sw_sh[2] - acc[0]) / p.d;
         a.rr = acc[1];
         a.rhs2 = acc[1];
         a.sp = acc[2];
@@ -282,58 +317,73 @@ __global__ void __launch_bounds__(256) k_anc_setup(Params p, const Real *A, cons
     }
 }
 
-// One CG pass per anchor (one block): q = G_m - colsum_m A_m - S_m (S_m . p_m) + lambda p,
-// a = rr / (p . q), x += a p, r -= a q, p = r + (rr'/rr) p; counts the anchors still active.
-template <typename Real>
-__global__ void __launch_bounds__(256) k_anc_cg(Params p, const Real *A, const Real *G,
-                                                const double *colsum, const double *S, Anchor *st,
-                                                double *x, double *r, double *pv, double *q,
-                                                Real *V, int *active)
+// One CG pass per anchor (one warp per anchor, kAncWarps anchors per block):
+// q = G_m - colsum_m A_m - S_m (S_m . p_m) + lambda p, a = rr / (p . q), x += a p,
+// r -= a q, p = r + (rr'/rr) p; counts the anchors still active.
+constexpr int kAncWarps = 8;
+__device__ __forceinline__ double wsum(double v)
 {
-    __shared__ double sm[32 * 3];
-    const int m = blockIdx.x;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename Real>
+__global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, int nsplit,
+                                                           const Real *A, const Real *G,
+                                                           const double *part, const double *S,
+                                                           Anchor *st, double *x, double *r,
+                                                           double *pv, double *q, Real *V,
+                                                           int *active)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kAncWarps + (threadIdx.x >> 5);
+    if (m >= p.M) return;
     Anchor &a = st[m];
     if (a.done) return;
-    const size_t o = (size_t)m * p.ld;
-    const double cs = colsum[m], sp = a.sp, lam = a.lam, rr = a.rr;
-    double b1[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        const double qi = (double)G[o + i] - cs * (double)A[o + i] - S[o + i] * sp + lam * pv[o + i];
+    double cs = 0.0;   // sum_j T_jm, row chunks in order (lane 0's sum is used)
+    for (int c = lane; c < nrc; c += 32) cs += part[((size_t)c * p.M + m) * 3];
+    cs = __shfl_sync(0xffffffffu, wsum(cs), 0);
+    const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
+    const double sp = a.sp, lam = a.lam, rr = a.rr;
+    double pq = 0.0;
+    for (int i = lane; i < p.ld; i += 32) {
+        double g = 0.0;
+        for (int z = 0; z < nsplit; ++z) g += (double)G[z * split + o + i];
+        const double qi = g - cs * (double)A[o + i] - S[o + i] * sp + lam * pv[o + i];
         q[o + i] = qi;
-        b1[0] += pv[o + i] * qi;
+        pq += pv[o + i] * qi;
     }
-    bsum(b1, sm);
-    const double pq = b1[0];
+    pq = __shfl_sync(0xffffffffu, wsum(pq), 0);
     if (!(pq > 0.0) || !isfinite(pq)) {
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             a.done = 1;
             if (!(rr <= p.cg_tol2 * a.rhs2)) a.status = FBSDE_ERR_CG;
         }
         return;
     }
     const double step = rr / pq;
-    double b2[1] = {0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+    double rn = 0.0;
+    for (int i = lane; i < p.ld; i += 32) {
         x[o + i] += step * pv[o + i];
         const double ri = r[o + i] - step * q[o + i];
         r[o + i] = ri;
-        b2[0] += ri * ri;
+        rn += ri * ri;
     }
-    bsum(b2, sm);
-    const double rr_new = b2[0], beta = rr_new / rr;
-    double b3[2] = {0.0, 0.0};
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+    const double rr_new = __shfl_sync(0xffffffffu, wsum(rn), 0), beta = rr_new / rr;
+    double b0 = 0.0, b1 = 0.0;
+    for (int i = lane; i < p.ld; i += 32) {
         const double pi = r[o + i] + beta * pv[o + i];
         pv[o + i] = pi;
         V[o + i] = (Real)pi;
-        b3[0] += S[o + i] * pi;
-        b3[1] += (double)A[o + i] * pi;
+        b0 += S[o + i] * pi;
+        b1 += (double)A[o + i] * pi;
     }
-    bsum(b3, sm);
-    if (threadIdx.x == 0) {
+    b0 = wsum(b0);
+    b1 = wsum(b1);
+    if (lane == 0) {
         a.rr = rr_new;
-        a.sp = b3[0];
-        a.ap = b3[1];
+        a.sp = b0;
+        a.ap = b1;
         a.iters += 1;
         if (rr_new <= p.cg_tol2 * a.rhs2) {
             a.done = 1;
@@ -414,6 +464,8 @@ struct Lay {
     int d, ld, N;
     int64_t M;
     size_t rs;   // bytes of one stream-precision value
+    int nrc, nsplit, kc;   // row chunks of the column pass; K splits (kc rows each) of the
+                           // tall contractions
     size_t P, A, YP, V, G1, W, T, G2, G3, S, rhs, x, r, pv, q, Y, Yn, pn, an, cs, st, cnt, total;
 };
 
@@ -432,6 +484,14 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.M = P->M;
     L.rs = P->precision == FBSDE_FP32 ? 4 : 8;
     const size_t M = (size_t)L.M, ld = (size_t)L.ld;
+    L.nrc = (int)((L.M + kRowChunk - 1) / kRowChunk);
+    {   // enough blocks for about two waves of the 152 SMs, at least 256 rows per split
+        const long long tiles = ((long long)(ld + 63) / 64) * ((L.M + 63) / 64);
+        const long long want = std::max(1ll, (2ll * 152 * 4 + tiles - 1) / tiles);
+        const long long ns = std::max(1ll, std::min(want, (long long)(L.M / 256)));
+        L.kc = (int)(((L.M + ns - 1) / ns + 15) / 16 * 16);
+        L.nsplit = (int)((L.M + L.kc - 1) / L.kc);   // every split holds rows
+    }
     size_t o = 0;
     auto take = [&](size_t b) { const size_t r = o; o = up(o + b); return r; };
     L.P = take(M * ld * L.rs);
@@ -441,8 +501,8 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.G1 = take(M * M * L.rs);
     L.W = take(M * M * L.rs);
     L.T = take(M * M * L.rs);
-    L.G2 = take(M * ld * L.rs);
-    L.G3 = take(M * ld * L.rs);
+    L.G2 = take((size_t)L.nsplit * M * ld * L.rs);
+    L.G3 = take((size_t)L.nsplit * M * ld * L.rs);
     L.S = take(M * ld * 8);
     L.rhs = take(M * ld * 8);
     L.x = take(M * ld * 8);
@@ -453,7 +513,7 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.Yn = take(M * 8);
     L.pn = take(M * 8);
     L.an = take(M * 8);
-    L.cs = take(M * 8);
+    L.cs = take((size_t)L.nrc * M * 3 * 8);
     L.st = take(M * sizeof(Anchor));
     L.cnt = take(2 * sizeof(int));
     L.total = o;
@@ -492,11 +552,11 @@ Params params_of(const fbsde_problem *P, const Lay &L, uint64_t seed)
 }
 
 template <typename Real, bool TN>
-cudaError_t gemm(int Mr, int Nc, int K, const Real *A, int lda, const Real *B, int ldb, Real *C,
-                 int ldc, cudaStream_t s)
+cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Real *B, int ldb,
+                 Real *C, int ldc, cudaStream_t s)
 {
-    const dim3 grid((Nc + 63) / 64, (Mr + 63) / 64);
-    k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, A, lda, B, ldb, C, ldc);
+    const dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, (K + kc - 1) / kc);
+    k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
     return cudaGetLastError();
 }
 
@@ -531,7 +591,7 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
     ANC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
     k_anc_terminal<Real><<<M, 128, 0, s>>>(p, x0, sidx, P, Y);
     ANC_TRY(cudaGetLastError());
-    const int colblocks = (M + 127) / 128;
+    const dim3 cgrid((M + 127) / 128, L.nrc);
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
         const double a = (double)k / (double)(k + 1), b = p.sigma * std::sqrt(p.dt * a);
@@ -539,22 +599,24 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         ANC_TRY(cudaGetLastError());
         k_anc_rows<Real><<<M, 128, 0, s>>>(p, P, A, Y, pn, an, YP);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, false>(M, M, ld, P, ld, A, ld, G1, M, s)));   // P A^T
+        ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, s)));   // P A^T
         const double rho_ref = p.sigma * p.sigma * p.d * (t_k + (k + 1) * p.dt);
-        k_anc_columns<Real><<<colblocks, 128, 0, s>>>(p, 0, rho_ref, G1, pn, an, Y, W, T, st, cs);
+        k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 0, rho_ref, G1, pn, an, Y, W, T, st, cs);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, true>(M, ld, M, W, M, P, ld, G2, ld, s)));    // W^T P
-        ANC_TRY((gemm<Real, true>(M, ld, M, W, M, YP, ld, G3, ld, s)));   // W^T (Y P)
-        k_anc_setup<Real><<<M, 256, 0, s>>>(p, A, G2, G3, cs, st, S, rhs, x, r, pv, V);
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, s)));    // W^T P
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, s)));   // W^T (Y P)
+        k_anc_setup<Real><<<M, 256, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S, rhs, x, r,
+                                           pv, V);
         ANC_TRY(cudaGetLastError());
         for (int it = 0; it < p.cg_max_iter; ++it) {
             const bool check = it % kCheckEvery == kCheckEvery - 1 || it + 1 == p.cg_max_iter;
             if (check) ANC_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));   // counts this pass
-            ANC_TRY((gemm<Real, false>(M, M, ld, P, ld, V, ld, G1, M, s)));   // U = P V^T
-            k_anc_columns<Real><<<colblocks, 128, 0, s>>>(p, 1, 0.0, G1, pn, an, Y, W, T, st, cs);
+            ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, s)));   // U = P V^T
+            k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, G1, pn, an, Y, W, T, st, cs);
             ANC_TRY(cudaGetLastError());
-            ANC_TRY((gemm<Real, true>(M, ld, M, T, M, P, ld, G2, ld, s)));    // G = T^T P
-            k_anc_cg<Real><<<M, 256, 0, s>>>(p, A, G2, cs, S, st, x, r, pv, q, V, cnt);
+            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, s)));   // T^T P
+            k_anc_cg<Real><<<(M + kAncWarps - 1) / kAncWarps, 32 * kAncWarps, 0, s>>>(
+                p, L.nrc, L.nsplit, A, G2, cs, S, st, x, r, pv, q, V, cnt);
             ANC_TRY(cudaGetLastError());
             if (check) {
                 ANC_TRY(cudaMemcpyAsync(host_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
