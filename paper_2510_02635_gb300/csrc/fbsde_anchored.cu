@@ -108,6 +108,74 @@ __global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, int kc,
     }
 }
 
+// FP32 variant with a 128 x 128 tile per block: 256 threads, each owning an 8 x 8 block
+// of outputs (rows 4 ty .. 4 ty + 3 and 64 + 4 ty .., columns likewise with tx), read from
+// shared memory four at a time.  Same layouts, split K and summation order rules as k_gemm.
+template <bool TN>
+__global__ void __launch_bounds__(256) k_gemm128(int Mr, int Nc, int K, int kc,
+                                                 const float *__restrict__ A, int lda,
+                                                 const float *__restrict__ B, int ldb,
+                                                 float *__restrict__ C, int ldc)
+{
+    constexpr int BM = 128, BN = 128, BK = 8, PAD = 4;
+    __shared__ __align__(16) float As[BK][BM + PAD];
+    __shared__ __align__(16) float Bs[BK][BN + PAD];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    C += (size_t)blockIdx.z * Mr * ldc;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            int kk, rr;
+            if (TN) { kk = e / BM; rr = e - kk * BM; }
+            else { rr = e / BK; kk = e - rr * BK; }
+            const int gr = r0 + rr, gk = k0 + kk;
+            float v = 0.0f;
+            if (gr < Mr && gk < ke) v = TN ? A[(size_t)gk * lda + gr] : A[(size_t)gr * lda + gk];
+            As[kk][rr] = v;
+            int cc;
+            if (TN) { kk = e / BN; cc = e - kk * BN; }
+            else { cc = e / BK; kk = e - cc * BK; }
+            const int gc = c0 + cc, gk2 = k0 + kk;
+            float w = 0.0f;
+            if (gc < Nc && gk2 < ke) w = TN ? B[(size_t)gk2 * ldb + gc] : B[(size_t)gc * ldb + gk2];
+            Bs[kk][cc] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = r0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+        if (r >= Mr) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = c0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+            if (c < Nc) C[(size_t)r * ldc + c] = acc[i][j];
+        }
+    }
+}
+
 // Fixed-order block sum of NV doubles (blockDim.x a multiple of 32, <= 1024).
 template <int NV> __device__ __forceinline__ void bsum(double (&v)[NV], double *sm)
 {
@@ -555,6 +623,13 @@ template <typename Real, bool TN>
 cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Real *B, int ldb,
                  Real *C, int ldc, cudaStream_t s)
 {
+    if constexpr (sizeof(Real) == 4) {
+        if (Mr >= 1024 && Nc >= 64) {   // large enough to fill the GPU with 128 x 128 tiles
+            const dim3 grid((Nc + 127) / 128, (Mr + 127) / 128, (K + kc - 1) / kc);
+            k_gemm128<TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
+            return cudaGetLastError();
+        }
+    }
     const dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, (K + kc - 1) / kc);
     k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
     return cudaGetLastError();
