@@ -531,13 +531,19 @@ def _main(argv=None) -> None:
     ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--cg-max-iter", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--x0", default="uniform", choices=["uniform", "zero"],
+                    help="query points: U[-1,1]^d from the seed, or the origin")
+    ap.add_argument("--anchored", action="store_true",
+                    help="Algorithm 1 with one regression per particle anchor "
+                         "(fbsde_solve_anchored)")
     ap.add_argument("--time-products", action="store_true",
                     help="run the launch profiler on the product kernel (the first "
                          "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
                          "one by one, outside CUDA graphs, e.g. for a kernel profiler)")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
-    x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)), device="cuda")
+    x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)) if a.x0 == "uniform"
+                      else np.zeros((a.Q, a.d)), device="cuda")
     theta = rng.uniform(0.5, 1.5, size=a.d) if a.kind in ("hjb_logquad", "affine_test") else None
     solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
                     theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
@@ -546,7 +552,8 @@ def _main(argv=None) -> None:
         fbsde_profile_select(["matvec"])
     for r in range(a.repeat):
         t0 = time.perf_counter()
-        out = solver.solve(x0, seed=a.seed)
+        out = (solve_anchored(solver.problem, x0, a.seed) if a.anchored
+               else solver.solve(x0, seed=a.seed))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
