@@ -103,10 +103,38 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_init(Params p, const double
     if (threadIdx.x == 0) st.abar = gsum;
 }
 
-// Adjoint CG set-up at level k: operator of the level-k regression (tape: S, lambda,
-// 1/W; weights via p.w), right-hand side alphaxbar - alphabar S, start from 0.
+// Starting guess of the adjoint solve of level k >= 1: the previous level's solution v
+// (still in slot 0; the level-to-level change of v is small), rounded for the product
+// k_matvec forms next (Gamma_c x needs sum_j w_j (D_j . x) D_j), and S . x.
 template <typename Real>
-__global__ void __launch_bounds__(kFinThreads) k_adj_setup(Params p)
+__global__ void __launch_bounds__(kFinThreads) k_adj_warm(Params p)
+{
+    __shared__ double sm[32 * 4];
+    const int s = blockIdx.x, k = p.level;
+    const WS<Real> ws(p);
+    const Tape tp(p);
+    SolveState &st = p.st[s];
+    const double *Sk = tp.S(s, k), *x = ws.v64(s, 0);
+    Real *pR = ws.vR(s, 0);
+    double a[1] = {0.0};
+    #pragma unroll 4
+    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+        pR[i] = (Real)x[i];
+        a[0] += Sk[i] * x[i];
+    }
+    block_sum(a, sm);
+    if (threadIdx.x == 0) {
+        st.sx = a[0];
+        st.done = 0;   // the product runs for every query
+    }
+}
+
+// Adjoint CG set-up at level k: operator of the level-k regression (tape: S, lambda,
+// 1/W; weights via p.w), right-hand side alphaxbar - alphabar S.  Start from 0, or with
+// warm = 1 from the guess of k_adj_warm, whose unnormalised product sum_j w_j (D_j . x) D_j
+// is in slot 5: r = rhs - (Gamma_c + lambda I) x.
+template <typename Real>
+__global__ void __launch_bounds__(kFinThreads) k_adj_setup(Params p, int warm)
 {
     __shared__ double sm[32 * 4];
     const int s = blockIdx.x, k = p.level;
@@ -115,30 +143,35 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_setup(Params p)
     SolveState &st = p.st[s];
     const double *Sk = tp.S(s, k), *ab = tp.av(s, 0);
     double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3);
+    const double *Gx = ws.v64(s, 5);
     Real *pR = ws.vR(s, 0);
     const double abar = st.abar;
-    double a[2] = {0.0, 0.0};  // |rhs|^2, S.rhs
+    const double *sc = tp.scal(s, k);
+    const double lam = sc[0], invW = sc[1], sx = st.sx;
+    double a[3] = {0.0, 0.0, 0.0};  // |rhs|^2, |r|^2, S.r
     #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         S[i] = Sk[i];
         const double rhs = ab[i] - abar * Sk[i];
-        x[i] = 0.0;
-        r[i] = rhs;
-        pp[i] = rhs;
-        pR[i] = (Real)rhs;
+        double ri = rhs;
+        if (warm) ri -= Gx[i] * invW - Sk[i] * sx + lam * x[i];
+        else x[i] = 0.0;
+        r[i] = ri;
+        pp[i] = ri;
+        pR[i] = (Real)ri;
         a[0] += rhs * rhs;
-        a[1] += Sk[i] * rhs;
+        a[1] += ri * ri;
+        a[2] += Sk[i] * ri;
     }
     block_sum(a, sm);
     if (threadIdx.x == 0) {
-        const double *sc = tp.scal(s, k);
-        st.lambda = sc[0];
-        st.invW = sc[1];
-        st.rr = a[0];
+        st.lambda = lam;
+        st.invW = invW;
+        st.rr = a[1];
         st.rhs2 = a[0];
-        st.sp = a[1];
+        st.sp = a[2];
         st.iters = 0;
-        st.done = (a[0] == 0.0) ? 1 : 0;
+        st.done = (a[1] <= p.cg_tol2 * a[0]) ? 1 : 0;
     }
 }
 

@@ -478,7 +478,12 @@ cudaError_t run_adjoint(Params p, const Layout &L, const double *x0, const doubl
                                      cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
                 return e;
         }
-        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_setup(p, L, s));
+        if (k >= 1) {   // start from the previous level's solution: one product
+            FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_warm(p, L, s));
+            FBSDE_TRY(FBSDE_K_MATVEC, LR::matvec(p, L, s));
+            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 1, 5, 0, s));
+        }
+        FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_setup(p, L, k >= 1 ? 1 : 0, s));
         if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_post(p, L, s));
         FBSDE_TRY(FBSDE_K_ADJOINT, LR::adj_rows(p, L, s));

@@ -47,6 +47,7 @@ struct SolveState {
     double abar, sv, sumz_l, zz_l;  // reverse sweep
     double rr_prev, cg_alpha;       // previous r . r and step of the CG recurrence
     double cg_beta, cg_step;        // scalars of the current CG pass
+    double sx;                      // S . x of the adjoint solve's starting guess
     int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive,
         arrive_q, cg_ok, pad4;
 };
@@ -114,7 +115,8 @@ template <typename Real> struct Launch {
                                void *out, cudaStream_t st);
     // reverse sweep
     static cudaError_t adj_init(const Params &p, const Layout &L, const double *ubar, cudaStream_t s);
-    static cudaError_t adj_setup(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_warm(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t adj_setup(const Params &p, const Layout &L, int warm, cudaStream_t s);
     static cudaError_t adj_post(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t adj_rows(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t adj_zlevel(const Params &p, const Layout &L, cudaStream_t s);

@@ -167,9 +167,16 @@ cudaError_t Launch<Real>::adj_init(const Params &p, const Layout &L, const doubl
 }
 
 template <typename Real>
-cudaError_t Launch<Real>::adj_setup(const Params &p, const Layout &L, cudaStream_t s)
+cudaError_t Launch<Real>::adj_warm(const Params &p, const Layout &L, cudaStream_t s)
 {
-    dev::k_adj_setup<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    dev::k_adj_warm<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::adj_setup(const Params &p, const Layout &L, int warm, cudaStream_t s)
+{
+    dev::k_adj_setup<Real><<<L.Q, kFinThreads, 0, s>>>(p, warm);
     return cudaGetLastError();
 }
 
