@@ -16,6 +16,11 @@
 // Newton (2.16)-(2.17) Y_k^m = alpha_m + dt f(t_k, X_k^m, Y_k^m, Z_k^m).  u(0,x0) is the
 // mean of Y_0^m; grad u(0,x0) = x of anchor 0 at k = 0 (every anchor is x0 there).
 // The particle paths are the solve's own (Brownian bridge, Philox normals).
+//
+// Kernels: the contractions of FP32 solves with M >= 1024 run on the tensor cores
+// (k_gemm_tc, split TF32, fbsde_tcgemm.cuh), the CG pass's P V^T with the column pass fused
+// into its epilogue; smaller or FP64 solves use the SIMT k_gemm and k_anc_columns.  The
+// per-anchor d-vector kernels (setup, CG pass, Newton) run one warp per anchor.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +29,7 @@
 #include <vector>
 
 #include "fbsde_kernels.cuh"
+#include "fbsde_tcgemm.cuh"
 
 namespace fbsde {
 namespace anchored {
@@ -103,74 +109,6 @@ __global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, int kc,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = c0 + tx + 16 * j;
-            if (c < Nc) C[(size_t)r * ldc + c] = acc[i][j];
-        }
-    }
-}
-
-// FP32 variant with a 128 x 128 tile per block: 256 threads, each owning an 8 x 8 block
-// of outputs (rows 4 ty .. 4 ty + 3 and 64 + 4 ty .., columns likewise with tx), read from
-// shared memory four at a time.  Same layouts, split K and summation order rules as k_gemm.
-template <bool TN>
-__global__ void __launch_bounds__(256) k_gemm128(int Mr, int Nc, int K, int kc,
-                                                 const float *__restrict__ A, int lda,
-                                                 const float *__restrict__ B, int ldb,
-                                                 float *__restrict__ C, int ldc)
-{
-    constexpr int BM = 128, BN = 128, BK = 8, PAD = 4;
-    __shared__ __align__(16) float As[BK][BM + PAD];
-    __shared__ __align__(16) float Bs[BK][BN + PAD];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
-    C += (size_t)blockIdx.z * Mr * ldc;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = threadIdx.x + 256 * u;
-            int kk, rr;
-            if (TN) { kk = e / BM; rr = e - kk * BM; }
-            else { rr = e / BK; kk = e - rr * BK; }
-            const int gr = r0 + rr, gk = k0 + kk;
-            float v = 0.0f;
-            if (gr < Mr && gk < ke) v = TN ? A[(size_t)gk * lda + gr] : A[(size_t)gr * lda + gk];
-            As[kk][rr] = v;
-            int cc;
-            if (TN) { kk = e / BN; cc = e - kk * BN; }
-            else { cc = e / BK; kk = e - cc * BK; }
-            const int gc = c0 + cc, gk2 = k0 + kk;
-            float w = 0.0f;
-            if (gc < Nc && gk2 < ke) w = TN ? B[(size_t)gk2 * ldb + gc] : B[(size_t)gc * ldb + gk2];
-            Bs[kk][cc] = w;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][4 * ty]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + 4 * ty]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + 4 * tx]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = r0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
-        if (r >= Mr) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = c0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
             if (c < Nc) C[(size_t)r * ldc + c] = acc[i][j];
         }
     }
@@ -322,59 +260,84 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, const Real *G,
     }
 }
 
-// Per anchor (one block): S, rhs, lambda, and the CG start x = 0, r = p = rhs.
+// Sum over the nsplit partial products X[z * split + ix], z in order, in the stream
+// precision (eight loads in flight): the partials are stream-precision sums themselves, and
+// on this part the FP64 pipe is a small fraction of the FP32 one.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_anc_setup(Params p, int nrc, int nsplit, const Real *A,
-                                                   const Real *G2, const Real *G3,
-                                                   const double *part, Anchor *st, double *S,
-                                                   double *rhs, double *x, double *r, double *pv,
-                                                   Real *V)
+__device__ __forceinline__ Real split_sum(const Real *X, size_t split, size_t ix, int nsplit)
 {
-    __shared__ double sm[32 * 4];
-    __shared__ double sw_sh[3];
-    const int m = blockIdx.x;
-    Anchor &a = st[m];
-    if (threadIdx.x == 0) {   // the column sums of the weights, chunks in order
-        double sw = 0.0, swy = 0.0, swr = 0.0;
-        for (int c = 0; c < nrc; ++c) {
-            const double *o = part + ((size_t)c * p.M + m) * 3;
-            sw += o[0];
-            swy += o[1];
-            swr += o[2];
-        }
-        sw_sh[0] = sw;
-        sw_sh[1] = swy / sw;
-        sw_sh[2] = swr / sw;
+    Real g = Real(0);
+    int z = 0;
+    for (; z + 8 <= nsplit; z += 8) {
+        Real t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = X[(z + u) * split + ix];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g += t[u];
     }
-    __syncthreads();
-    const double invW = 1.0 / sw_sh[0], c = sw_sh[1];
+    for (; z < nsplit; ++z) g += X[z * split + ix];
+    return g;
+}
+
+// The per-anchor d-vector kernels run one warp per anchor, kAncWarps anchors per block, with
+// warp-only tree sums: on this part the FP64 pipe is a small fraction of the FP32 one, and
+// block-wide FP64 reductions repeated by every thread cost more than the element work.
+constexpr int kAncWarps = 8;
+template <int NV> __device__ __forceinline__ void warp_sums(double (&v)[NV])
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
+// Per anchor: S, rhs, lambda, and the CG start x = 0, r = p = rhs.
+template <typename Real>
+__global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc, int nsplit,
+                                                              const Real *A, const Real *G2,
+                                                              const Real *G3, const double *part,
+                                                              Anchor *st, double *S, double *rhs,
+                                                              double *x, double *r, double *pv,
+                                                              Real *V)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kAncWarps + (threadIdx.x >> 5);
+    if (m >= p.M) return;
+    Anchor &a = st[m];
+    double w[3] = {0.0, 0.0, 0.0};   // column sums of the weights: lane-strided chunks in
+                                     // order, then the warp tree
+    for (int c = lane; c < nrc; c += 32) {
+        const double *o = part + ((size_t)c * p.M + m) * 3;
+        w[0] += o[0];
+        w[1] += o[1];
+        w[2] += o[2];
+    }
+    warp_sums(w);
+    const double invW = 1.0 / w[0], cm = w[1] / w[0];
     const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // |S|^2, |rhs|^2, S . rhs, A . rhs
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
-        double g2 = 0.0, g3 = 0.0;
-        for (int z = 0; z < nsplit; ++z) {
-            g2 += (double)G2[z * split + o + i];
-            g3 += (double)G3[z * split + o + i];
-        }
-        g2 *= invW;
-        const double s = g2 - (double)A[o + i];
-        const double b = g3 * invW - c * g2;
-        S[o + i] = s;
+    for (int i = lane; i < p.ld; i += 32) {
+        const double g2 = (double)split_sum(G2, split, o + i, nsplit) * invW;
+        const double g3 = (double)split_sum(G3, split, o + i, nsplit);
+        const double ai = (double)A[o + i];
+        const double sv = g2 - ai;
+        const double b = g3 * invW - cm * g2;
+        S[o + i] = sv;
         rhs[o + i] = b;
         x[o + i] = 0.0;
         r[o + i] = b;
         pv[o + i] = b;
         V[o + i] = (Real)b;
-        acc[0] += s * s;
+        acc[0] += sv * sv;
         acc[1] += b * b;
-        acc[2] += s * b;
-        acc[3] += (double)A[o + i] * b;
+        acc[2] += sv * b;
+        acc[3] += ai * b;
     }
-    bsum(acc, sm);
-    if (threadIdx.x == 0) {
-        a.W = sw_sh[0];
-        a.c = c;
-        a.lam = p.ridge_rel * (sw_sh[2] - acc[0]) / p.d;
+    warp_sums(acc);
+    if (lane == 0) {
+        a.W = w[0];
+        a.c = cm;
+        a.lam = p.ridge_rel * (w[2] * invW - acc[0]) / p.d;
         a.rr = acc[1];
         a.rhs2 = acc[1];
         a.sp = acc[2];
@@ -385,16 +348,10 @@ __global__ void __launch_bounds__(256) k_anc_setup(Params p, int nrc, int nsplit
     }
 }
 
-// One CG pass per anchor (one warp per anchor, kAncWarps anchors per block):
+// One CG pass per anchor:
 // q = G_m - colsum_m A_m - S_m (S_m . p_m) + lambda p, a = rr / (p . q), x += a p,
-// r -= a q, p = r + (rr'/rr) p; counts the anchors still active.
-constexpr int kAncWarps = 8;
-__device__ __forceinline__ double wsum(double v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// r -= a q, p = r + (rr'/rr) p; counts the anchors still active.  G_m is the sum of the
+// nsplit partial products (split_sum).
 template <typename Real>
 __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, int nsplit,
                                                            const Real *A, const Real *G,
@@ -408,50 +365,49 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
     if (m >= p.M) return;
     Anchor &a = st[m];
     if (a.done) return;
-    double cs = 0.0;   // sum_j T_jm, row chunks in order (lane 0's sum is used)
-    for (int c = lane; c < nrc; c += 32) cs += part[((size_t)c * p.M + m) * 3];
-    cs = __shfl_sync(0xffffffffu, wsum(cs), 0);
+    double cs[1] = {0.0};   // sum_j T_jm: lane-strided row chunks in order, then the warp tree
+    for (int c = lane; c < nrc; c += 32) cs[0] += part[((size_t)c * p.M + m) * 3];
+    warp_sums(cs);
     const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
     const double sp = a.sp, lam = a.lam, rr = a.rr;
-    double pq = 0.0;
+    double pq[1] = {0.0};
     for (int i = lane; i < p.ld; i += 32) {
-        double g = 0.0;
-        for (int z = 0; z < nsplit; ++z) g += (double)G[z * split + o + i];
-        const double qi = g - cs * (double)A[o + i] - S[o + i] * sp + lam * pv[o + i];
+        const double g = (double)split_sum(G, split, o + i, nsplit);
+        const double qi = g - cs[0] * (double)A[o + i] - S[o + i] * sp + lam * pv[o + i];
         q[o + i] = qi;
-        pq += pv[o + i] * qi;
+        pq[0] += pv[o + i] * qi;
     }
-    pq = __shfl_sync(0xffffffffu, wsum(pq), 0);
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    warp_sums(pq);
+    if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
         if (lane == 0) {
             a.done = 1;
             if (!(rr <= p.cg_tol2 * a.rhs2)) a.status = FBSDE_ERR_CG;
         }
         return;
     }
-    const double step = rr / pq;
-    double rn = 0.0;
+    const double step = rr / pq[0];
+    double rn[1] = {0.0};
     for (int i = lane; i < p.ld; i += 32) {
         x[o + i] += step * pv[o + i];
         const double ri = r[o + i] - step * q[o + i];
         r[o + i] = ri;
-        rn += ri * ri;
+        rn[0] += ri * ri;
     }
-    const double rr_new = __shfl_sync(0xffffffffu, wsum(rn), 0), beta = rr_new / rr;
-    double b0 = 0.0, b1 = 0.0;
+    warp_sums(rn);
+    const double rr_new = rn[0], beta = rr_new / rr;
+    double b[2] = {0.0, 0.0};
     for (int i = lane; i < p.ld; i += 32) {
         const double pi = r[o + i] + beta * pv[o + i];
         pv[o + i] = pi;
         V[o + i] = (Real)pi;
-        b0 += S[o + i] * pi;
-        b1 += (double)A[o + i] * pi;
+        b[0] += S[o + i] * pi;
+        b[1] += (double)A[o + i] * pi;
     }
-    b0 = wsum(b0);
-    b1 = wsum(b1);
+    warp_sums(b);
     if (lane == 0) {
         a.rr = rr_new;
-        a.sp = b0;
-        a.ap = b1;
+        a.sp = b[0];
+        a.ap = b[1];
         a.iters += 1;
         if (rr_new <= p.cg_tol2 * a.rhs2) {
             a.done = 1;
@@ -464,28 +420,30 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
     }
 }
 
-// Per anchor (one block): alpha = c - S . x (Eq. 3.20), Z = sigma x, the features of f at
-// (t_k, X_k^m, Z) and Newton (2.16)-(2.17) for Y_k^m.
+// Per anchor: alpha = c - S . x (Eq. 3.20), Z = sigma x, the features of f at
+// (t_k, X_k^m, Z) and Newton (2.16)-(2.17) for Y_k^m (lane 0).
 template <typename Real>
-__global__ void __launch_bounds__(256) k_anc_newton(Params p, double t_k, const double *x0,
-                                                    const Real *A, const double *S,
-                                                    const double *x, Anchor *st, double *Ynew,
-                                                    int *status)
+__global__ void __launch_bounds__(32 * kAncWarps) k_anc_newton(Params p, double t_k,
+                                                               const double *x0, const Real *A,
+                                                               const double *S, const double *x,
+                                                               Anchor *st, double *Ynew,
+                                                               int *status)
 {
-    __shared__ double sm[32 * 4];
-    const int m = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kAncWarps + (threadIdx.x >> 5);
+    if (m >= p.M) return;
     Anchor &a = st[m];
     const size_t o = (size_t)m * p.ld;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // S . x, sum cos(x0 + A), sum x, |x|^2
-    for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
+    for (int i = lane; i < p.ld; i += 32) {
         const double xi = x[o + i];
         acc[0] += S[o + i] * xi;
-        if (i < p.d) acc[1] += cos(x0[i] + (double)A[o + i]);
+        if (i < p.d) acc[1] += (double)dev::cos_stream((Real)x0[i] + A[o + i]);
         acc[2] += xi;
         acc[3] += xi * xi;
     }
-    bsum(acc, sm);
-    if (threadIdx.x == 0) {
+    warp_sums(acc);
+    if (lane == 0) {
         const double alpha = a.c - acc[0];
         a.alpha = alpha;
         const double feat = dev::f_feature(p, t_k, acc[1], p.sigma * acc[2],
@@ -553,10 +511,10 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.rs = P->precision == FBSDE_FP32 ? 4 : 8;
     const size_t M = (size_t)L.M, ld = (size_t)L.ld;
     L.nrc = (int)((L.M + kRowChunk - 1) / kRowChunk);
-    {   // enough blocks for about two waves of the 152 SMs, at least 256 rows per split
+    {   // enough blocks for about two waves of the 152 SMs, at least 128 rows per split
         const long long tiles = ((long long)(ld + 63) / 64) * ((L.M + 63) / 64);
         const long long want = std::max(1ll, (2ll * 152 * 4 + tiles - 1) / tiles);
-        const long long ns = std::max(1ll, std::min(want, (long long)(L.M / 256)));
+        const long long ns = std::max(1ll, std::min(want, (long long)(L.M / 128)));
         L.kc = (int)(((L.M + ns - 1) / ns + 15) / 16 * 16);
         L.nsplit = (int)((L.M + L.kc - 1) / L.kc);   // every split holds rows
     }
@@ -619,16 +577,86 @@ Params params_of(const fbsde_problem *P, const Lay &L, uint64_t seed)
     return p;
 }
 
+// Epilogue of the CG pass's product U = P V^T on the tensor cores: in place of U, the
+// matrix T_jm = w_jm (U_jm - A_m . v_m) / W_m of the next product and its column sums
+// over each 128-row tile (k_anc_columns in mode 1, fused; same FP32 arithmetic).  Anchors
+// that are done keep their old column of T.
+struct TcColumnsEpi {
+    const float *W;
+    float *T;
+    const Anchor *st;
+    double *part;
+    int M;
+    static constexpr bool kColSums = true;
+    struct Col {
+        float ap, inv;
+        int skip;
+    };
+    struct Pre {
+        float w[32];   // W_jm of the 32 rows a warp hands out
+    };
+    __device__ __forceinline__ void prefetch(int j0, int m, const Col &, Pre &pr) const
+    {
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+            pr.w[rr] = (m >= 0 && j0 + rr < M) ? W[(size_t)(j0 + rr) * M + m] : 0.0f;
+    }
+    __device__ __forceinline__ Col column(int m) const
+    {
+        Col c{0.0f, 0.0f, 1};
+        if (m >= 0) {
+            const Anchor &a = st[m];
+            c.skip = a.done;
+            c.ap = (float)a.ap;
+            c.inv = (float)(1.0 / a.W);
+        }
+        return c;
+    }
+    __device__ __forceinline__ float put(int, int j, int m, float u, const Col &c, const Pre &pr,
+                                         int rr) const
+    {
+        if (c.skip) return 0.0f;
+        const float t = pr.w[rr] * (u - c.ap) * c.inv;
+        T[(size_t)j * M + m] = t;
+        return t;
+    }
+    __device__ __forceinline__ void colsum(int tile, int m, float s) const
+    {
+        part[((size_t)tile * M + m) * 3] = (double)s;
+    }
+};
+
+// The FP32 products of M >= 1024 particles go to the tensor cores (k_gemm_tc, split
+// TF32); the k-contiguous layout there needs 16-byte rows and k ranges in steps of 4.
+inline bool tc_layout_ok(bool tn, int K, int kc, const void *A, int lda, const void *B, int ldb)
+{
+    if (tn) return true;
+    return K % 4 == 0 && kc % 4 == 0 && lda % 4 == 0 && ldb % 4 == 0 &&
+           reinterpret_cast<uintptr_t>(A) % 16 == 0 && reinterpret_cast<uintptr_t>(B) % 16 == 0;
+}
+
+template <bool TN, class Epi>
+cudaError_t gemm_tc(int Mr, int Nc, int K, int kc, const float *A, int lda, const float *B,
+                    int ldb, const Epi &epi, int *status, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(dev::k_gemm_tc<TN, Epi>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dev::kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((Nc + dev::kTcBN - 1) / dev::kTcBN, (Mr + dev::kTcBM - 1) / dev::kTcBM,
+                    (K + kc - 1) / kc);
+    dev::k_gemm_tc<TN, Epi><<<grid, dev::kTcThreads, dev::kTcSmemBytes, s>>>(Mr, Nc, K, kc, A, lda,
+                                                                           B, ldb, epi, status);
+    return cudaGetLastError();
+}
+
 template <typename Real, bool TN>
 cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Real *B, int ldb,
-                 Real *C, int ldc, cudaStream_t s)
+                 Real *C, int ldc, int *status, cudaStream_t s)
 {
     if constexpr (sizeof(Real) == 4) {
-        if (Mr >= 1024 && Nc >= 64) {   // large enough to fill the GPU with 128 x 128 tiles
-            const dim3 grid((Nc + 127) / 128, (Mr + 127) / 128, (K + kc - 1) / kc);
-            k_gemm128<TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
-            return cudaGetLastError();
-        }
+        if (Mr >= 1024 && tc_layout_ok(TN, K, kc, A, lda, B, ldb))
+            return gemm_tc<TN>(Mr, Nc, K, kc, A, lda, B, ldb, dev::TcStore{C, Mr, ldc}, status, s);
     }
     const dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, (K + kc - 1) / kc);
     k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
@@ -667,6 +695,11 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
     k_anc_terminal<Real><<<M, 128, 0, s>>>(p, x0, sidx, P, Y);
     ANC_TRY(cudaGetLastError());
     const dim3 cgrid((M + 127) / 128, L.nrc);
+    const int awarps = (M + kAncWarps - 1) / kAncWarps;   // blocks of the per-anchor kernels
+    // FP32 with M >= 1024: the CG pass's column pass runs in the tensor-core product's
+    // epilogue, with column sums over 128-row tiles
+    const bool fused = sizeof(Real) == 4 && M >= 1024 && tc_layout_ok(false, ld, ld, P, ld, A, ld);
+    const int nrc_fused = (M + dev::kTcBM - 1) / dev::kTcBM;
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
         const double a = (double)k / (double)(k + 1), b = p.sigma * std::sqrt(p.dt * a);
@@ -674,24 +707,30 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         ANC_TRY(cudaGetLastError());
         k_anc_rows<Real><<<M, 128, 0, s>>>(p, P, A, Y, pn, an, YP);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, s)));   // P A^T
+        ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, cnt + 1, s)));   // P A^T
         const double rho_ref = p.sigma * p.sigma * p.d * (t_k + (k + 1) * p.dt);
         k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 0, rho_ref, G1, pn, an, Y, W, T, st, cs);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, s)));    // W^T P
-        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, s)));   // W^T (Y P)
-        k_anc_setup<Real><<<M, 256, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S, rhs, x, r,
-                                           pv, V);
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, cnt + 1, s)));    // W^T P
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, cnt + 1, s)));   // W^T (Y P)
+        k_anc_setup<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S,
+                                                           rhs, x, r, pv, V);
         ANC_TRY(cudaGetLastError());
         for (int it = 0; it < p.cg_max_iter; ++it) {
             const bool check = it % kCheckEvery == kCheckEvery - 1 || it + 1 == p.cg_max_iter;
             if (check) ANC_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));   // counts this pass
-            ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, s)));   // U = P V^T
-            k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, G1, pn, an, Y, W, T, st, cs);
-            ANC_TRY(cudaGetLastError());
-            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, s)));   // T^T P
-            k_anc_cg<Real><<<(M + kAncWarps - 1) / kAncWarps, 32 * kAncWarps, 0, s>>>(
-                p, L.nrc, L.nsplit, A, G2, cs, S, st, x, r, pv, q, V, cnt);
+            if (fused) {   // T and its column sums straight from the product's epilogue
+                if constexpr (sizeof(Real) == 4)
+                    ANC_TRY((gemm_tc<false>(M, M, ld, ld, P, ld, V, ld,
+                                            TcColumnsEpi{W, T, st, cs, M}, cnt + 1, s)));
+            } else {
+                ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, s)));   // U = P V^T
+                k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, G1, pn, an, Y, W, T, st, cs);
+                ANC_TRY(cudaGetLastError());
+            }
+            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, s)));   // T^T P
+            k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, s>>>(
+                p, fused ? nrc_fused : L.nrc, L.nsplit, A, G2, cs, S, st, x, r, pv, q, V, cnt);
             ANC_TRY(cudaGetLastError());
             if (check) {
                 ANC_TRY(cudaMemcpyAsync(host_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -699,7 +738,7 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
                 if (*host_cnt == 0) break;   // every anchor converged (or failed)
             }
         }
-        k_anc_newton<Real><<<M, 256, 0, s>>>(p, t_k, x0, A, S, x, st, Yn, cnt + 1);
+        k_anc_newton<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, t_k, x0, A, S, x, st, Yn, cnt + 1);
         ANC_TRY(cudaGetLastError());
         std::swap(P, A);   // level k's rows are the cloud of level k-1
         std::swap(Y, Yn);

@@ -1,7 +1,8 @@
 """Algorithm 1 with one regression per particle anchor: the CUDA path against the oracle's
 literal per-anchor solve on the same seeds (FP64 within 1e-10, FP32 within 1e-4), and, with
 uniform weights, against the single-anchor entry point.  Sizes are ragged with respect to
-the 64 x 64 tiles of the contractions and the 16-byte row chunks."""
+the 64 x 64 tiles of the SIMT contractions, the 128 x 128 tiles of the tensor-core ones
+(M >= 1024, FP32) and the 16-byte row chunks."""
 import math
 
 import numpy as np
@@ -62,6 +63,18 @@ def test_fp64_matches_oracle(kind, d, M, N, extra):
 def test_fp32_matches_oracle(kind, d, M, N, extra):
     from paper_2510_02635_gb300 import fbsde as fb
     out, refs, *_ = _run(fb, kind, d, M, N, "fp32", extra)
+    _check(out, refs, TOL_FP32)
+
+
+@pytest.mark.parametrize("kind,d,M,N,extra", [
+    ("ac_manufactured", 21, 1030, 2, {}),
+    ("logistic_grad", 12, 1100, 2, {"sigma": 12.0, "T": 1.0}),
+])
+def test_fp32_tensor_core_products_match_oracle(kind, d, M, N, extra):
+    """From M = 1024 particles on, the FP32 contractions run on the tensor cores (split
+    TF32); M is ragged with respect to their 128 x 128 tiles and 16-wide k stages."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, kind, d, M, N, "fp32", extra, Q=1)
     _check(out, refs, TOL_FP32)
 
 
