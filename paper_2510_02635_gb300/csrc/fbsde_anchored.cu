@@ -587,7 +587,7 @@ struct TcColumnsEpi {
     const Anchor *st;
     double *part;
     int M;
-    static constexpr bool kColSums = true;
+    static constexpr bool kColSums = true, kPrefetch = true;
     struct Col {
         float ap, inv;
         int skip;

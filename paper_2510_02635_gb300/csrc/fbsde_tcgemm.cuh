@@ -12,11 +12,12 @@
 // order of the FP32 rounding of a length-100 dot product.
 //
 // Tile: 128 rows (tensor-memory lanes) x 128 columns (tensor-memory columns), 16 values of
-// k per pipeline stage, two stages, 256 threads.  All threads load and split the next
-// stage into registers while the tensor core runs the current one; one thread issues the
-// MMAs and commits them to the stage's mbarrier, whose completion frees the stage.  Three
-// blocks fit on an SM (64 KB of shared memory, 128 tensor-memory columns each), so one
-// block's loads overlap another's MMAs.
+// k per pipeline stage, two stages, 256 threads.  All threads load the stage after next
+// into registers and split the next one into shared memory while the tensor core runs the
+// current one; one thread issues the MMAs and commits them to the stage's mbarrier, whose
+// completion frees the stage.  Two blocks
+// are resident per SM (64 KB of shared memory and 128 tensor-memory columns each; registers
+// for two), so one block's loads overlap another's MMAs.
 //
 // Shared-memory operand layout (K-major, no swizzle): the tile of 128 rows x 16 k is four
 // 16-byte chunks of k; chunk c of row r is at c * 2048 + r * 16 bytes.  In the terms of the
@@ -156,7 +157,7 @@ __device__ __forceinline__ void tc_store(const float4 (&v)[2], uint8_t *hi, uint
 struct TcStore {
     float *C;
     int Mr, ldc;
-    static constexpr bool kColSums = false;
+    static constexpr bool kColSums = false, kPrefetch = false;
     struct Col {};
     struct Pre {};
     __device__ __forceinline__ Col column(int) const { return {}; }
@@ -182,7 +183,7 @@ struct TcStore {
 // Grid (ceil(Nc / 128), ceil(Mr / 128), splits), kTcThreads threads, kTcSmemBytes of
 // dynamic shared memory.  A wait that times out sets *status = FBSDE_ERR_TIMEOUT (if 0).
 template <bool TN, class Epi>
-__global__ void __launch_bounds__(kTcThreads, 3)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_gemm_tc(int Mr, int Nc, int K, int kc, const float *__restrict__ A, int lda,
               const float *__restrict__ B, int ldb, Epi epi, int *status)
 {
@@ -212,12 +213,18 @@ __global__ void __launch_bounds__(kTcThreads, 3)
     const uint32_t tmem = *tslot;
 
     bool timed_out = false;
-    float4 va[2], vb[2];
+    // Raw values of the next two stages in registers (even and odd steps): a stage's loads
+    // are issued two steps before it is stored, so their latency spans two steps.
+    float4 va0[2], vb0[2], va1[2], vb1[2];
     if (nk > 0) {
-        tc_load<TN>(va, A, lda, r0, Mr, kb, ke);
-        tc_load<TN>(vb, B, ldb, c0, Nc, kb, ke);
+        tc_load<TN>(va0, A, lda, r0, Mr, kb, ke);
+        tc_load<TN>(vb0, B, ldb, c0, Nc, kb, ke);
     }
-    for (int t = 0; t < nk; ++t) {
+    if (nk > 1) {
+        tc_load<TN>(va1, A, lda, r0, Mr, kb + kTcBK, ke);
+        tc_load<TN>(vb1, B, ldb, c0, Nc, kb + kTcBK, ke);
+    }
+    auto step = [&](int t, float4 (&va)[2], float4 (&vb)[2]) {
         const int b = t & 1;
         uint8_t *stg = tsm + b * kTcStageBytes;
         // the stage's previous MMAs (step t - 2) must be done before it is overwritten
@@ -226,8 +233,8 @@ __global__ void __launch_bounds__(kTcThreads, 3)
         tc_store(vb, stg + 2 * kTcPartBytes, stg + 3 * kTcPartBytes);
         fence_async_smem();
         __syncthreads();
-        if (t + 1 < nk) {   // next stage's loads overlap this stage's MMAs
-            const int k0 = kb + (t + 1) * kTcBK;
+        if (t + 2 < nk) {   // loads of step t + 2 overlap this step's MMAs and the next step
+            const int k0 = kb + (t + 2) * kTcBK;
             tc_load<TN>(va, A, lda, r0, Mr, k0, ke);
             tc_load<TN>(vb, B, ldb, c0, Nc, k0, ke);
         }
@@ -244,6 +251,10 @@ __global__ void __launch_bounds__(kTcThreads, 3)
             }
             tc_commit(&bar[b]);
         }
+    };
+    for (int t = 0; t < nk; t += 2) {
+        step(t, va0, vb0);
+        if (t + 1 < nk) step(t + 1, va1, vb1);
     }
     if (nk > 0) mbar_wait_or_flag(&bar[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u, timed_out);
     tc_fence_after();
@@ -272,11 +283,20 @@ __global__ void __launch_bounds__(kTcThreads, 3)
         for (int j = 0; j < 32; ++j) scr[lane * 33 + j] = __uint_as_float(v[j]);
         __syncwarp();
         float sum = 0.0f;
+        if constexpr (Epi::kPrefetch) {   // pre is indexed by rr: unroll fully
 #pragma unroll
-        for (int rr = 0; rr < 32; ++rr) {
-            const int row = r0 + 32 * q + rr;
-            if (row < Mr && cc < Nc)
-                sum += epi.put(blockIdx.z, row, cc, scr[rr * 33 + lane], cst, pre, rr);
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = r0 + 32 * q + rr;
+                if (row < Mr && cc < Nc)
+                    sum += epi.put(blockIdx.z, row, cc, scr[rr * 33 + lane], cst, pre, rr);
+            }
+        } else {
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = r0 + 32 * q + rr;
+                if (row < Mr && cc < Nc)
+                    sum += epi.put(blockIdx.z, row, cc, scr[rr * 33 + lane], cst, pre, rr);
+            }
         }
         if (Epi::kColSums) csm[q * kTcBN + col + lane] = sum;
         __syncwarp();
