@@ -1,8 +1,9 @@
 """Pins of the oracle's literal Algorithm 1 (one regression per particle anchor):
 the uniform-kernel limit equals the single-anchor solve (a shift of the regressors moves
 only the intercept), the affine problem's closed recursion holds for any kernel weights,
-and on the manufactured Allen-Cahn problem the per-particle anchors remove the bias that
-a single anchor leaves when f depends on x."""
+on the manufactured Allen-Cahn problem the per-particle anchors remove the bias that
+a single anchor leaves when f depends on x, and at tiny sizes the solve equals a brute
+force of the definitions (dense least squares per anchor)."""
 import math
 
 import numpy as np
@@ -70,3 +71,68 @@ def test_per_particle_anchors_remove_the_single_anchor_bias():
     assert a["status"] == 0
     assert abs(a["u0"] - exact) < 2e-3
     assert abs(b["u0"] - exact) > 5 * abs(a["u0"] - exact)
+
+
+def _brute_force_anchored(p, x0, seed, s):
+    """Algorithm 1 with one regression per particle anchor, from the definitions at tiny
+    sizes: the particle paths, then per level and anchor m the Gaussian weights of
+    D_j = X_{k+1}^j - X_k^m with eps_k^2 = h^2 sigma^2 d (t_k + t_{k+1}) (normalised), the
+    weighted least squares of Y_{k+1} on [1, D] with the ridge lambda = ridge_rel tr(Gamma_c)/d
+    on the slope only (Remark 2.2) solved by a dense lstsq of the augmented system, the
+    anchor's intercept and Z = sigma slope, and Newton on Y = alpha + dt f (Eq. 2.16) to
+    full precision."""
+    d, N, M = p.d, p.N, p.M
+    dt = p.T / N
+    X = np.stack([oracle.path(p, x0, seed, s, j) for j in range(M)], axis=1)   # [N+1, M, d]
+    Y = np.array([oracle.g(p, X[N, j]) for j in range(M)])
+    slope0 = None
+    for k in range(N - 1, -1, -1):
+        t_k = k * dt
+        rho_ref = p.sigma ** 2 * d * (t_k + (k + 1) * dt)
+        Yk = np.empty(M)
+        for m in range(M):
+            D = X[k + 1] - X[k, m]
+            rho = np.sum(D * D, axis=1)
+            w = np.exp(-(rho - rho_ref) / (p.h ** 2 * rho_ref))
+            w /= w.sum()
+            S = w @ D
+            lam = p.ridge_rel * (w @ rho - S @ S) / d
+            sw = np.sqrt(w)
+            rows = np.vstack([np.hstack([sw[:, None], sw[:, None] * D]),
+                              np.hstack([np.zeros((d, 1)), math.sqrt(lam) * np.eye(d)])])
+            rhs = np.concatenate([sw * Y, np.zeros(d)])
+            coef = np.linalg.lstsq(rows, rhs, rcond=None)[0]
+            alpha, slope = coef[0], coef[1:]
+            z = p.sigma * slope
+            y = alpha
+            for _ in range(100):
+                fv, dfdy = oracle.f(p, t_k, X[k, m], y, z)
+                step = (y - alpha - dt * fv) / (1.0 - dt * dfdy)
+                y -= step
+                if abs(step) <= 1e-15 * max(1.0, abs(y)):
+                    break
+            Yk[m] = y
+            if k == 0 and m == 0:
+                slope0 = slope
+        Y = Yk
+    return float(Y.mean()), slope0
+
+
+@pytest.mark.parametrize("kind,extra", [
+    ("ac_manufactured", {}),
+    ("logistic_grad", {"sigma": 3.0, "T": 1.0}),
+    ("hjb_logquad", {"sigma": math.sqrt(2.0), "T": 1.0}),
+])
+def test_per_anchor_solve_equals_dense_least_squares_brute_force(kind, extra):
+    """Same u(0,x0) and grad u as the brute force above (1e-10 relative): the per-anchor
+    bandwidth, the normalisation, the ridge, the intercept and Newton per anchor."""
+    d, N, M = 3, 3, 40
+    rng = np.random.default_rng(11)
+    theta = rng.uniform(0.5, 1.5, d) if kind == "hjb_logquad" else None
+    x0 = rng.normal(scale=0.5, size=d)
+    p = _p(kind, d, N, M, 2.0, theta=theta, **extra)
+    ref_u, ref_g = _brute_force_anchored(p, x0, 3, 1)
+    a = oracle.solve_anchored(p, x0, 3, 1)
+    assert a["status"] == 0
+    assert abs(a["u0"] - ref_u) <= 1e-10 * max(1.0, abs(ref_u)), (a["u0"], ref_u)
+    assert np.max(np.abs(a["grad"] - ref_g)) <= 1e-9 * max(1.0, np.max(np.abs(ref_g)))
