@@ -1,6 +1,7 @@
 """End-to-end pins of the oracle's Algorithm 1 against results the paper or the
 mathematics fix: exact closed forms of the discrete scheme, a value the paper prints,
-an exact Monte-Carlo representation (Cole-Hopf) and the first-order time convergence.
+an exact Monte-Carlo representation (Cole-Hopf), the first-order time convergence, and at
+tiny sizes a brute force of the definitions with nonlinear drivers.
 """
 import math
 import os
@@ -248,3 +249,67 @@ def test_bridge_path_ends_and_levels():
     assert np.array_equal(a[0], x0)
     b = oracle.path(p, x0, 4, 2, 5)
     assert np.all(np.abs(a[1:] - b[1:]) > 0)
+
+
+def _brute_force_single_anchor(p, x0, seed, s):
+    """Algorithm 1 with one anchor per level (the query's drift path a_k = x0), from the
+    definitions at tiny sizes: the particle paths; per level the Gaussian weights of
+    D_j = X_{k+1}^j - x0 with eps_k^2 = h^2 sigma^2 d t_{k+1} (normalised), the weighted
+    least squares of Y_{k+1} on [1, D] with the ridge lambda = ridge_rel tr(Gamma_c)/d on the
+    slope only, solved by a dense lstsq of the augmented system; Z_k = sigma slope; and per
+    particle Newton on Y = alpha + slope . (X_k^j - x0) + dt f(t_k, X_k^j, Y, Z_k)."""
+    d, N, M = p.d, p.N, p.M
+    dt = p.T / N
+    X = np.stack([oracle.path(p, x0, seed, s, j) for j in range(M)], axis=1)   # [N+1, M, d]
+    Y = np.array([oracle.g(p, X[N, j]) for j in range(M)])
+    slope = None
+    for k in range(N - 1, -1, -1):
+        t_k = k * dt
+        rho_ref = p.sigma ** 2 * d * (k + 1) * dt
+        D = X[k + 1] - x0
+        rho = np.sum(D * D, axis=1)
+        w = np.exp(-(rho - rho_ref) / (p.h ** 2 * rho_ref)) if math.isfinite(p.h) else np.ones(M)
+        w /= w.sum()
+        S = w @ D
+        lam = p.ridge_rel * (w @ rho - S @ S) / d
+        sw = np.sqrt(w)
+        rows = np.vstack([np.hstack([sw[:, None], sw[:, None] * D]),
+                          np.hstack([np.zeros((d, 1)), math.sqrt(lam) * np.eye(d)])])
+        coef = np.linalg.lstsq(rows, np.concatenate([sw * Y, np.zeros(d)]), rcond=None)[0]
+        alpha, slope = coef[0], coef[1:]
+        z = p.sigma * slope
+        Yk = np.empty(M)
+        for j in range(M):
+            e = alpha + slope @ (X[k, j] - x0)
+            y = e
+            for _ in range(100):
+                fv, dfdy = oracle.f(p, t_k, X[k, j], y, z)
+                step = (y - e - dt * fv) / (1.0 - dt * dfdy)
+                y -= step
+                if abs(step) <= 1e-15 * max(1.0, abs(y)):
+                    break
+            Yk[j] = y
+        Y = Yk
+    return float(Y.mean()), slope
+
+
+@pytest.mark.parametrize("kind,extra", [
+    ("ac_manufactured", {}),
+    ("logistic_grad", {"sigma": 3.0, "T": 1.0}),
+    ("hjb_logquad", {"sigma": math.sqrt(2.0), "T": 1.0}),
+    ("ac_doublewell", {"sigma": math.sqrt(2.0), "T": 0.3}),
+])
+def test_solve_equals_dense_least_squares_brute_force(kind, extra):
+    """Nonlinear drivers: orc_solve equals the brute force above to 1e-10 (the bandwidth,
+    the normalisation, the ridge on the slope only, the prediction at X_k^j and Newton)."""
+    d, N, M = 4, 4, 60
+    rng = np.random.default_rng(17)
+    theta = rng.uniform(0.5, 1.5, d) if kind == "hjb_logquad" else None
+    x0 = rng.normal(scale=0.5, size=d)
+    sigma, T = extra.get("sigma", 1.0), extra.get("T", 0.5)
+    p = _prob(kind, d, sigma, T, N, M, theta=theta, h=2.0, cg_tol=1e-14)
+    ref_u, ref_g = _brute_force_single_anchor(p, x0, 5, 2)
+    r = oracle.solve(p, x0, 5, 2)
+    assert r["status"] == 0
+    assert abs(r["u0"] - ref_u) <= 1e-10 * max(1.0, abs(ref_u)), (r["u0"], ref_u)
+    assert np.max(np.abs(r["grad"] - ref_g)) <= 1e-9 * max(1.0, np.max(np.abs(ref_g)))
