@@ -202,15 +202,13 @@ __global__ void __launch_bounds__(256) k_adj_rows(Params p)
     const WS<Real> ws(p);
     const int lane = threadIdx.x & 31;
     const int nch = p.ld / E;
-    const long long items = (long long)p.Q * p.M * p.nseg;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const bool cos_feature = p.kind == FBSDE_AC_MANUFACTURED;
-    for (long long it = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; it < items;
-         it += nwarps) {
-        const int seg = (int)(it % p.nseg);
-        const long long row = it / p.nseg;
-        const int s = (int)(row / p.M);
-        const long long j = row - (long long)s * p.M;
+    for (RowItems w(p, (((unsigned long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5,
+                    (unsigned long long)nwarps);
+         w.s < (uint32_t)p.Q; w.next()) {
+        const int seg = (int)w.seg, s = (int)w.s;
+        const long long j = w.j;
         const Real *vr = ws.vR(s, 1), *x0r = ws.vR(s, 2);
         const Real *drow = ws.row(s, j);
         Real acc[3] = {Real(0), Real(0), Real(0)};
