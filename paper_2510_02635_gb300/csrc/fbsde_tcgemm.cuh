@@ -15,9 +15,11 @@
 // k per pipeline stage, two stages, 256 threads.  All threads load the stage after next
 // into registers and split the next one into shared memory while the tensor core runs the
 // current one; one thread issues the MMAs and commits them to the stage's mbarrier, whose
-// completion frees the stage.  Two blocks
-// are resident per SM (64 KB of shared memory and 128 tensor-memory columns each; registers
-// for two), so one block's loads overlap another's MMAs.
+// completion frees the stage.  Two or three
+// blocks are resident per SM (64 KB of shared memory and 128 tensor-memory columns each;
+// the launch bounds keep registers for two), so one block's loads overlap another's MMAs.
+// Shared memory caps an SM at three blocks, 384 of its 512 tensor-memory columns, so the
+// allocation never waits for another block to free columns.
 //
 // Shared-memory operand layout (K-major, no swizzle): the tile of 128 rows x 16 k is four
 // 16-byte chunks of k; chunk c of row r is at c * 2048 + r * 16 bytes.  In the terms of the
