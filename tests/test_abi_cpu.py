@@ -109,3 +109,78 @@ def test_solve_argument_errors_return_synchronously(lib):
     assert L.fbsde_philox4x32_10(None, None, None, 4, None) == 1
     assert L.fbsde_normals(0, 0, 0, 0, 4, 0, 0, fake, None) == 1
     assert L.fbsde_normals(0, 0, 0, 0, 4, 8, 3, fake, None) == 1
+
+
+def test_anchored_workspace_sizing(lib):
+    """Three M x M stream-precision matrices dominate at large M (the rest is O(M d) plus
+    the M^2/64 column-pass partials); M beyond 32768 (or below 2) and invalid problems
+    give 0."""
+    for M in (2048, 16384):
+        n = fbsde.fbsde_anchored_workspace_bytes(_prob(M=M))
+        assert n >= 3 * M * M * 4
+    n16 = fbsde.fbsde_anchored_workspace_bytes(_prob(M=16384))
+    assert n16 < 1.1 * 3 * 16384 ** 2 * 4
+    n32 = fbsde.fbsde_anchored_workspace_bytes(_prob(M=32768))
+    assert 3.8 < n32 / n16 < 4.1
+    assert fbsde.fbsde_anchored_workspace_bytes(_prob(M=2048, precision="fp64")) >= 3 * 2048 ** 2 * 8
+    assert fbsde.fbsde_anchored_workspace_bytes(_prob(M=32768)) > 0
+    for bad in (dict(M=32769), dict(M=1), dict(sigma=0.0), dict(d=0)):
+        assert fbsde.fbsde_anchored_workspace_bytes(_prob(**bad)) == 0
+
+
+def test_anchored_argument_errors_return_synchronously(lib):
+    p = _prob(M=256)
+    n = fbsde.fbsde_anchored_workspace_bytes(p)
+    fake, unaligned = C.c_void_p(1 << 20), C.c_void_p((1 << 20) + 8)
+    L = lib
+    assert L.fbsde_solve_anchored(C.byref(p), 1, None, 0, 0, fake, None, fake, n, None) == 1
+    assert L.fbsde_solve_anchored(C.byref(p), 1, fake, 0, 0, None, None, fake, n, None) == 1
+    assert L.fbsde_solve_anchored(C.byref(p), 0, fake, 0, 0, fake, None, fake, n, None) == 1
+    ph = _prob(kind="hjb_logquad", M=256)
+    assert L.fbsde_solve_anchored(C.byref(ph), 1, fake, 0, 0, fake, None, fake, 1 << 40, None) == 1
+    assert L.fbsde_solve_anchored(C.byref(p), 1, fake, 0, 0, fake, None, None, n, None) == 2
+    assert L.fbsde_solve_anchored(C.byref(p), 1, fake, 0, 0, fake, None, fake, n - 1, None) == 2
+    assert L.fbsde_solve_anchored(C.byref(p), 1, fake, 0, 0, fake, None, unaligned, n, None) == 2
+
+
+def test_adjoint_workspace_and_argument_errors(lib):
+    """The adjoint workspace holds the solve's plus the tape; theta_bar only for kinds with
+    terminal coefficients; theta required for them; workspace checks as for the solve."""
+    p = _prob(M=512, N=6)
+    ns, na = fbsde.fbsde_workspace_bytes(p, 2), fbsde.fbsde_adjoint_workspace_bytes(p, 2)
+    assert na > ns
+    assert na - ns >= 6 * 2 * 512 * 4   # per level and query: the M taped weights at least
+    assert fbsde.fbsde_adjoint_workspace_bytes(_prob(sigma=-1.0), 1) == 0
+    fake, L = C.c_void_p(1 << 20), lib
+    args = lambda pr, **kw: [C.byref(pr), 1, kw.get("x0", fake), 0, 0, kw.get("ub", fake), fake,
+                             None, kw.get("xb", fake), kw.get("tb"), kw.get("ws", fake),
+                             kw.get("n", 1 << 40), None]
+    assert L.fbsde_adjoint(*args(p, x0=None)) == 1
+    assert L.fbsde_adjoint(*args(p, ub=None)) == 1
+    assert L.fbsde_adjoint(*args(p, xb=None)) == 1
+    assert L.fbsde_adjoint(*args(p, tb=fake)) == 1            # no theta in this kind
+    assert L.fbsde_adjoint(*args(_prob(kind="hjb_logquad"))) == 1   # theta missing
+    na1 = fbsde.fbsde_adjoint_workspace_bytes(p, 1)   # the calls above and below use Q = 1
+    assert L.fbsde_adjoint(*args(p, ws=None)) == 2
+    assert L.fbsde_adjoint(*args(p, n=na1 - 1)) == 2
+    assert L.fbsde_adjoint(*args(p, ws=C.c_void_p((1 << 20) + 16), n=na1)) == 2
+
+
+def test_plan_workspace_is_the_aligned_sum_of_the_instances(lib):
+    fake = (1 << 20)
+    pa, pb = _prob(M=512), _prob(d=37, M=300, precision="fp64")
+    arr = (fbsde.fbsde_instance * 2)()
+    arr[0] = fbsde.fbsde_instance(pa, 2, 0, 1, fake, fake, None)
+    arr[1] = fbsde.fbsde_instance(pb, 1, 0, 2, fake, fake, fake)
+    total = int(lib.fbsde_plan_workspace_bytes(2, arr))
+    a, b = fbsde.fbsde_workspace_bytes(pa, 2), fbsde.fbsde_workspace_bytes(pb, 1)
+    up = lambda x: (x + 255) // 256 * 256
+    assert total == up(up(a) + b)
+    assert int(lib.fbsde_plan_workspace_bytes(0, arr)) == 0
+    arr[1] = fbsde.fbsde_instance(pb, 1, 0, 2, None, fake, None)   # x0 missing
+    assert int(lib.fbsde_plan_workspace_bytes(2, arr)) == 0
+    h = C.c_void_p()
+    assert lib.fbsde_plan_create(None, 1, arr, 0, None, 0) == 1
+    assert lib.fbsde_plan_create(C.byref(h), 1, arr, 0, None, 0) == 2
+    assert lib.fbsde_plan_create(C.byref(h), 1, arr, 0, C.c_void_p(fake), up(a) - 1) == 2
+    assert h.value is None
