@@ -199,14 +199,17 @@ FBSDE_API int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const doubl
  * Lemma 3.7 / Remark 2.2 per anchor, Z_k^m = sigma alpha_x^m, and Newton (2.16)-(2.17)
  * with the anchor's own intercept alpha^m and Z_k^m.  u(0,x0) = mean_m Y_0^m; grad_u0 is
  * alpha_x at k = 0 (all anchors are x0 there).  Cost O(M^2 d) per level and CG pass: the
- * M regressions share two M x M x d contractions per pass.  With uniform weights
- * (h <= 0 or inf) the result equals fbsde_solve's up to rounding.
+ * M regressions share two M x M x d contractions per pass.  With FP32 and M >= 1024 these
+ * run on the tensor cores with the FP32 operands split into TF32 hi and lo parts (about
+ * 1e-6 relative per product); FP64 and smaller M use FP32/FP64 SIMT products.  With uniform
+ * weights (h <= 0 or inf) the result equals fbsde_solve's up to rounding.
  *   Same arguments as fbsde_solve (no trace); M <= 32768; theta (if the kind needs it)
  *   is a device pointer in P->theta; workspace >= fbsde_anchored_workspace_bytes(P)
  *   bytes, 256-byte aligned, reused for the Q queries one after the other.
  * The call blocks the host: it reads the count of anchors still iterating every four CG
  * passes.  Returns FBSDE_OK, an argument error, or the first device status (FBSDE_ERR_CG,
- * FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE).
+ * FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE, or FBSDE_ERR_TIMEOUT when a tensor-core pipeline
+ * wait ran out).
  */
 FBSDE_API size_t fbsde_anchored_workspace_bytes(const fbsde_problem *P);
 FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
