@@ -103,7 +103,7 @@ def _load():
                                                C.c_uint32, _dp, _dp]
             lib.orc_solve_anchored.restype = C.c_int
             lib.orc_adjoint.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, _dp,
-                                        _dp, _dp]
+                                        _dp, _dp, _dp]
             lib.orc_adjoint.restype = C.c_int
             lib.orc_path.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, C.c_int64,
                                      _dp]
@@ -314,13 +314,18 @@ def f_grads(prob: Problem, t: float, x, y: float, z) -> tuple[np.ndarray, np.nda
     return fx, fz
 
 
-def adjoint(prob: Problem, x0, seed: int, solve_index: int = 0) -> dict:
+def adjoint(prob: Problem, x0, seed: int, solve_index: int = 0, trace: bool = False) -> dict:
     """Reverse-mode derivatives of the estimator u(0,x0) with respect to x0 and theta for
-    the same random increments (a plain tape over the levels of Algorithm 1)."""
+    the same random increments (a plain tape over the levels of Algorithm 1).  With trace,
+    also v_levels [N, d]: the solution of each level's adjoint regression solve."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     u0 = C.c_double(math.nan)
     dx, dth = np.zeros(prob.d), np.zeros(prob.d)
+    vl = np.full((prob.N, prob.d), np.nan) if trace else None
     ps = prob.c_struct()
     st = _load().orc_adjoint(C.byref(ps), _ptr(x0), int(seed), int(solve_index), C.byref(u0),
-                             _ptr(dx), _ptr(dth))
-    return {"u0": float(u0.value), "du_dx0": dx, "du_dtheta": dth, "status": int(st)}
+                             _ptr(dx), _ptr(dth), _ptr(vl))
+    out = {"u0": float(u0.value), "du_dx0": dx, "du_dtheta": dth, "status": int(st)}
+    if trace:
+        out["v_levels"] = vl
+    return out

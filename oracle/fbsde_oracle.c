@@ -819,10 +819,11 @@ static int gamma_c_solve(int d, int64_t M, const double *D, const double *w, con
  *   Ybar_{k+1}^j = w_j (alphabar + (D_j - S_k) . v),  D_j = X_{k+1}^j - x0,
  * then x0bar += sum_j Ybar_N^j grad g(X_N^j), thetabar = sum_j Ybar_N^j d_theta g(X_N^j).
  * The kernel weights and the ridge depend only on D_j, which does not move with x0.
- * Outputs u0, du_dx0[d], du_dtheta[d] (may be NULL).
+ * Outputs u0, du_dx0[d], du_dtheta[d] (may be NULL), and v_levels[N][d] (may be NULL):
+ * the solution v of level k's adjoint regression solve, a trace for tests.
  */
 int orc_adjoint(const orc_problem *P, const double *x0, uint64_t seed, uint32_t solve_index,
-                double *u0, double *du_dx0, double *du_dtheta)
+                double *u0, double *du_dx0, double *du_dtheta, double *v_levels)
 {
     const int d = P->d, N = P->N;
     const int64_t M = P->M;
@@ -944,6 +945,8 @@ int orc_adjoint(const orc_problem *P, const double *x0, uint64_t seed, uint32_t 
             goto done;
         }
         if (st != ORC_OK && status == ORC_OK) status = st;
+        if (v_levels)
+            for (int i = 0; i < d; ++i) v_levels[(size_t)k * d + i] = v[i];
         const double sv = dotd(d, S, v);
         for (int64_t j = 0; j < M; ++j) {
             double dv = 0.0;

@@ -124,3 +124,29 @@ def test_problem_table_derivatives_match_numerical_differentiation(kind):
             pm = oracle.Problem(kind, d, 0.8, 1.0, 4, 16, theta=tm)
             assert gt[i] == pytest.approx((oracle.g(pp, x) - oracle.g(pm, x)) / (2 * h),
                                           rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("kind,d,M,sigma,T", [
+    ("hjb_logquad", 200, 800, math.sqrt(2.0), 1.0),
+    ("ac_manufactured", 200, 800, 1.0, 1.0),
+])
+def test_adjoint_solution_moves_between_levels(kind, d, M, sigma, T):
+    """The adjoint regression's solution v changes by a large fraction from one level to
+    the next (its right-hand side sums per-particle noise), unlike the primal alpha_x; a
+    start from the previous level's v saves few CG passes and a linear extrapolation over two
+    levels is worse.  This is why the GPU reverse sweep needs about twice the primal's CG
+    passes."""
+    N = 20
+    rng = np.random.default_rng(1)
+    theta = rng.uniform(0.5, 1.5, d) if kind == "hjb_logquad" else None
+    x0 = rng.normal(scale=1 / math.sqrt(d), size=d)
+    p = oracle.Problem(kind, d, sigma, T, N, M, theta=theta, cg_tol=1e-12)
+    V = oracle.adjoint(p, x0, 4, 0, trace=True)["v_levels"]
+    const = [np.linalg.norm(V[k] - V[k - 1]) / np.linalg.norm(V[k]) for k in range(2, N)]
+    linear = [np.linalg.norm(V[k] - 2 * V[k - 1] + V[k - 2]) / np.linalg.norm(V[k])
+              for k in range(2, N)]
+    assert 0.2 < np.median(const) < 0.8
+    assert np.median(linear) > np.median(const)
+    prim = oracle.solve(p, x0, 4, 0, trace=True)["alpha_x"]
+    steady = [np.linalg.norm(prim[k] - prim[k + 1]) / np.linalg.norm(prim[k]) for k in range(N - 1)]
+    assert np.median(steady) < np.median(const)
