@@ -102,6 +102,12 @@ def _load():
             lib.orc_solve_anchored.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64,
                                                C.c_uint32, _dp, _dp]
             lib.orc_solve_anchored.restype = C.c_int
+            lib.orc_solve_neighbours.argtypes = [C.POINTER(_Problem), C.c_int64, _dp, C.c_uint64,
+                                                 C.c_uint32, _dp, _dp]
+            lib.orc_solve_neighbours.restype = C.c_int
+            lib.orc_solve_batch.argtypes = [C.POINTER(_Problem), C.c_int64, _dp, C.c_uint64,
+                                            C.c_uint32, _dp, _dp]
+            lib.orc_solve_batch.restype = C.c_int
             lib.orc_adjoint.argtypes = [C.POINTER(_Problem), _dp, C.c_uint64, C.c_uint32, _dp,
                                         _dp, _dp, _dp]
             lib.orc_adjoint.restype = C.c_int
@@ -292,6 +298,33 @@ def solve_anchored(prob: Problem, x0, seed: int, solve_index: int = 0) -> dict:
     ps = prob.c_struct()
     st = _load().orc_solve_anchored(C.byref(ps), _ptr(x0), int(seed), int(solve_index),
                                     C.byref(u0), _ptr(grad))
+    return {"u0": float(u0.value), "grad": grad, "status": int(st)}
+
+
+def solve_neighbours(prob: Problem, K: int, x0, seed: int, solve_index: int = 0) -> dict:
+    """Algorithm 1 with one regression per particle anchor over the anchor's K nearest
+    particles only (the subset reading of Remark 2.1).  K = M is solve_anchored."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    assert x0.shape == (prob.d,)
+    u0 = C.c_double(math.nan)
+    grad = np.zeros(prob.d)
+    ps = prob.c_struct()
+    st = _load().orc_solve_neighbours(C.byref(ps), int(K), _ptr(x0), int(seed), int(solve_index),
+                                      C.byref(u0), _ptr(grad))
+    return {"u0": float(u0.value), "grad": grad, "status": int(st)}
+
+
+def solve_batch(prob: Problem, K: int, x0, seed: int, solve_index: int = 0) -> dict:
+    """Algorithm 1 with one regression per particle anchor over a batch of K particles, the
+    cyclic window j = (m + q) mod M of anchor m (the random-batch reading of Remark 2.1; the
+    paths are i.i.d., so the window is a random batch in law).  K = M is solve_anchored."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    assert x0.shape == (prob.d,)
+    u0 = C.c_double(math.nan)
+    grad = np.zeros(prob.d)
+    ps = prob.c_struct()
+    st = _load().orc_solve_batch(C.byref(ps), int(K), _ptr(x0), int(seed), int(solve_index),
+                                 C.byref(u0), _ptr(grad))
     return {"u0": float(u0.value), "grad": grad, "status": int(st)}
 
 

@@ -701,6 +701,193 @@ done:
     return status;
 }
 
+/*
+ * Algorithm 1 with one regression per particle anchor over the anchor's K nearest
+ * particles only (Remark 2.1: a small subset of the nearest particles instead of all of
+ * them; the random-batch reading keeps the cost O(M K d) per level).  As
+ * orc_solve_anchored, except that for anchor m the regression runs over the K indices j
+ * with the smallest |X_{k+1}^j - X_k^m|^2, ties broken by the smaller j, with the Gaussian
+ * weights normalised over that subset.  K = M is orc_solve_anchored.
+ */
+typedef struct {
+    double rho;
+    int64_t j;
+} orc_nb;
+
+static int nb_cmp(const void *a, const void *b)
+{
+    const orc_nb *x = (const orc_nb *)a, *y = (const orc_nb *)b;
+    if (x->rho < y->rho) return -1;
+    if (x->rho > y->rho) return 1;
+    return x->j < y->j ? -1 : (x->j > y->j ? 1 : 0);
+}
+
+int orc_solve_neighbours(const orc_problem *P, int64_t K, const double *x0, uint64_t seed,
+                         uint32_t solve_index, double *u0, double *grad_u0)
+{
+    const int d = P->d, N = P->N;
+    const int64_t M = P->M;
+    if (d < 1 || N < 1 || M < 2 || K < 2 || K > M || !(P->T > 0.0) || !(P->sigma > 0.0))
+        return ORC_ERR_ARG;
+    if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta)
+        return ORC_ERR_ARG;
+    const double dt = P->T / N;
+    const size_t Md = (size_t)M * (size_t)d;
+    double *Xn = (double *)malloc(sizeof(double) * Md);
+    double *Xk = (double *)malloc(sizeof(double) * Md);
+    double *D = (double *)malloc(sizeof(double) * (size_t)K * d);
+    double *Ys = (double *)malloc(sizeof(double) * K);
+    double *Y = (double *)malloc(sizeof(double) * M);
+    double *Yk = (double *)malloc(sizeof(double) * M);
+    double *ax = (double *)malloc(sizeof(double) * d);
+    double *z = (double *)malloc(sizeof(double) * d);
+    double *xi = (double *)malloc(sizeof(double) * d);
+    orc_nb *nb = (orc_nb *)malloc(sizeof(orc_nb) * M);
+    int status = ORC_OK;
+    if (!Xn || !Xk || !D || !Ys || !Y || !Yk || !ax || !z || !xi || !nb) {
+        status = ORC_ERR_NOMEM;
+        goto done;
+    }
+    for (int64_t j = 0; j < M; ++j) {
+        path_end(P, x0, seed, solve_index, j, Xn + j * (int64_t)d, xi);
+        Y[j] = orc_g(P, Xn + j * (int64_t)d);
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        const double t_k = k * dt;
+        for (int64_t j = 0; j < M; ++j)
+            path_step(P, k, x0, seed, solve_index, j, Xn + j * (int64_t)d, Xk + j * (int64_t)d, xi);
+        const double rho_ref = P->sigma * P->sigma * d * (t_k + (k + 1) * dt);
+        for (int64_t m = 0; m < M; ++m) {
+            const double *a = Xk + m * (int64_t)d;
+            for (int64_t j = 0; j < M; ++j) {
+                double rho = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    const double e = Xn[j * (int64_t)d + i] - a[i];
+                    rho += e * e;
+                }
+                nb[j].rho = rho;
+                nb[j].j = j;
+            }
+            qsort(nb, (size_t)M, sizeof(orc_nb), nb_cmp);
+            for (int64_t q = 0; q < K; ++q) {
+                const int64_t j = nb[q].j;
+                for (int i = 0; i < d; ++i) D[q * (int64_t)d + i] = Xn[j * (int64_t)d + i] - a[i];
+                Ys[q] = Y[j];
+            }
+            double alpha;
+            int cg_it = 0;
+            const int st = orc_llr(d, K, D, Ys, rho_ref, P->h, P->ridge_rel, P->cg_tol,
+                                   P->cg_max_iter, &alpha, ax, NULL, &cg_it);
+            if (st == ORC_ERR_NOMEM || st == ORC_ERR_ARG) {
+                status = st;
+                goto done;
+            }
+            if (st != ORC_OK && status == ORC_OK) status = st;
+            for (int i = 0; i < d; ++i) z[i] = P->sigma * ax[i];
+            const double feat = orc_f_feature(P, t_k, a, z);
+            int it;
+            Yk[m] = orc_newton(P, alpha, dt, feat, &it);
+            if (it < 0 && status == ORC_OK) status = ORC_ERR_NEWTON;
+            if (k == 0 && m == 0 && grad_u0) memcpy(grad_u0, ax, sizeof(double) * d);
+        }
+        memcpy(Y, Yk, sizeof(double) * M);
+        double *tmp = Xn;
+        Xn = Xk;
+        Xk = tmp;
+    }
+    {
+        double s = 0.0;
+        for (int64_t m = 0; m < M; ++m) s += Y[m];
+        if (u0) *u0 = s / M;
+        if (!isfinite(s / M) && status == ORC_OK) status = ORC_ERR_NONFINITE;
+    }
+done:
+    free(Xn); free(Xk); free(D); free(Ys); free(Y); free(Yk); free(ax); free(z); free(xi);
+    free(nb);
+    return status;
+}
+
+/*
+ * Algorithm 1 with one regression per particle anchor over a batch of K particles (the
+ * random-batch reading of Remark 2.1, after Jin, Li and Liu 2020): for anchor m the batch
+ * is the cyclic window j = (m + q) mod M, q = 0..K-1.  The particle paths are independent
+ * and identically distributed and the window does not depend on them, so it is a random
+ * batch in law; the Gaussian weights are normalised over the batch.  K = M is
+ * orc_solve_anchored up to the order of the sums.
+ */
+int orc_solve_batch(const orc_problem *P, int64_t K, const double *x0, uint64_t seed,
+                    uint32_t solve_index, double *u0, double *grad_u0)
+{
+    const int d = P->d, N = P->N;
+    const int64_t M = P->M;
+    if (d < 1 || N < 1 || M < 2 || K < 2 || K > M || !(P->T > 0.0) || !(P->sigma > 0.0))
+        return ORC_ERR_ARG;
+    if ((P->kind == ORC_HJB_LOGQUAD || P->kind == ORC_AFFINE_TEST) && !P->theta)
+        return ORC_ERR_ARG;
+    const double dt = P->T / N;
+    const size_t Md = (size_t)M * (size_t)d;
+    double *Xn = (double *)malloc(sizeof(double) * Md);
+    double *Xk = (double *)malloc(sizeof(double) * Md);
+    double *D = (double *)malloc(sizeof(double) * (size_t)K * d);
+    double *Ys = (double *)malloc(sizeof(double) * K);
+    double *Y = (double *)malloc(sizeof(double) * M);
+    double *Yk = (double *)malloc(sizeof(double) * M);
+    double *ax = (double *)malloc(sizeof(double) * d);
+    double *z = (double *)malloc(sizeof(double) * d);
+    double *xi = (double *)malloc(sizeof(double) * d);
+    int status = ORC_OK;
+    if (!Xn || !Xk || !D || !Ys || !Y || !Yk || !ax || !z || !xi) {
+        status = ORC_ERR_NOMEM;
+        goto done;
+    }
+    for (int64_t j = 0; j < M; ++j) {
+        path_end(P, x0, seed, solve_index, j, Xn + j * (int64_t)d, xi);
+        Y[j] = orc_g(P, Xn + j * (int64_t)d);
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        const double t_k = k * dt;
+        for (int64_t j = 0; j < M; ++j)
+            path_step(P, k, x0, seed, solve_index, j, Xn + j * (int64_t)d, Xk + j * (int64_t)d, xi);
+        const double rho_ref = P->sigma * P->sigma * d * (t_k + (k + 1) * dt);
+        for (int64_t m = 0; m < M; ++m) {
+            const double *a = Xk + m * (int64_t)d;
+            for (int64_t q = 0; q < K; ++q) {
+                const int64_t j = (m + q) % M;
+                for (int i = 0; i < d; ++i) D[q * (int64_t)d + i] = Xn[j * (int64_t)d + i] - a[i];
+                Ys[q] = Y[j];
+            }
+            double alpha;
+            int cg_it = 0;
+            const int st = orc_llr(d, K, D, Ys, rho_ref, P->h, P->ridge_rel, P->cg_tol,
+                                   P->cg_max_iter, &alpha, ax, NULL, &cg_it);
+            if (st == ORC_ERR_NOMEM || st == ORC_ERR_ARG) {
+                status = st;
+                goto done;
+            }
+            if (st != ORC_OK && status == ORC_OK) status = st;
+            for (int i = 0; i < d; ++i) z[i] = P->sigma * ax[i];
+            const double feat = orc_f_feature(P, t_k, a, z);
+            int it;
+            Yk[m] = orc_newton(P, alpha, dt, feat, &it);
+            if (it < 0 && status == ORC_OK) status = ORC_ERR_NEWTON;
+            if (k == 0 && m == 0 && grad_u0) memcpy(grad_u0, ax, sizeof(double) * d);
+        }
+        memcpy(Y, Yk, sizeof(double) * M);
+        double *tmp = Xn;
+        Xn = Xk;
+        Xk = tmp;
+    }
+    {
+        double s = 0.0;
+        for (int64_t m = 0; m < M; ++m) s += Y[m];
+        if (u0) *u0 = s / M;
+        if (!isfinite(s / M) && status == ORC_OK) status = ORC_ERR_NONFINITE;
+    }
+done:
+    free(Xn); free(Xk); free(D); free(Ys); free(Y); free(Yk); free(ax); free(z); free(xi);
+    return status;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Derivatives of the problem table used by the adjoint.                      */
 /* ------------------------------------------------------------------------- */

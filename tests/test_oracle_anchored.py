@@ -3,7 +3,9 @@ the uniform-kernel limit equals the single-anchor solve (a shift of the regresso
 only the intercept), the affine problem's closed recursion holds for any kernel weights,
 on the manufactured Allen-Cahn problem the per-particle anchors remove the bias that
 a single anchor leaves when f depends on x, and at tiny sizes the solve equals a brute
-force of the definitions (dense least squares per anchor)."""
+force of the definitions (dense least squares per anchor).  The same pins hold for the
+regressions over a subset of K particles per anchor (Remark 2.1: nearest subset, and the
+random batch as a cyclic window), plus the nearest subset's bias against the batch."""
 import math
 
 import numpy as np
@@ -73,7 +75,7 @@ def test_per_particle_anchors_remove_the_single_anchor_bias():
     assert abs(b["u0"] - exact) > 5 * abs(a["u0"] - exact)
 
 
-def _brute_force_anchored(p, x0, seed, s):
+def _brute_force_anchored(p, x0, seed, s, select=None):
     """Algorithm 1 with one regression per particle anchor, from the definitions at tiny
     sizes: the particle paths, then per level and anchor m the Gaussian weights of
     D_j = X_{k+1}^j - X_k^m with eps_k^2 = h^2 sigma^2 d (t_k + t_{k+1}) (normalised), the
@@ -93,6 +95,11 @@ def _brute_force_anchored(p, x0, seed, s):
         for m in range(M):
             D = X[k + 1] - X[k, m]
             rho = np.sum(D * D, axis=1)
+            if select is not None:   # regression over a subset of the particles
+                idx = select(m, rho)
+                D, rho, Ysub = D[idx], rho[idx], Y[idx]
+            else:
+                Ysub = Y
             w = np.exp(-(rho - rho_ref) / (p.h ** 2 * rho_ref))
             w /= w.sum()
             S = w @ D
@@ -100,7 +107,7 @@ def _brute_force_anchored(p, x0, seed, s):
             sw = np.sqrt(w)
             rows = np.vstack([np.hstack([sw[:, None], sw[:, None] * D]),
                               np.hstack([np.zeros((d, 1)), math.sqrt(lam) * np.eye(d)])])
-            rhs = np.concatenate([sw * Y, np.zeros(d)])
+            rhs = np.concatenate([sw * Ysub, np.zeros(d)])
             coef = np.linalg.lstsq(rows, rhs, rcond=None)[0]
             alpha, slope = coef[0], coef[1:]
             z = p.sigma * slope
@@ -136,3 +143,59 @@ def test_per_anchor_solve_equals_dense_least_squares_brute_force(kind, extra):
     assert a["status"] == 0
     assert abs(a["u0"] - ref_u) <= 1e-10 * max(1.0, abs(ref_u)), (a["u0"], ref_u)
     assert np.max(np.abs(a["grad"] - ref_g)) <= 1e-9 * max(1.0, np.max(np.abs(ref_g)))
+
+
+# Regression over a subset of K particles per anchor (Remark 2.1): the K nearest (ties by
+# the smaller index) or the cyclic window j = (m + q) mod M (a random batch in law).
+def _nearest(K):
+    return lambda m, rho: np.lexsort((np.arange(len(rho)), rho))[:K]
+
+
+def _window(K, M):
+    return lambda m, rho: (m + np.arange(K)) % M
+
+
+@pytest.mark.parametrize("which", ["nearest", "batch"])
+def test_subset_solves_with_all_particles_equal_the_per_anchor_solve(which):
+    d, N, M = 5, 3, 90
+    x0 = np.random.default_rng(2).normal(scale=0.4, size=d)
+    for kind, extra in (("ac_manufactured", {}), ("logistic_grad", {"sigma": 3.0, "T": 1.0})):
+        p = _p(kind, d, N, M, 2.0, **extra)
+        fn = oracle.solve_neighbours if which == "nearest" else oracle.solve_batch
+        a, b = fn(p, M, x0, 7, 1), oracle.solve_anchored(p, x0, 7, 1)
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["u0"] - b["u0"]) <= 1e-11 * max(1.0, abs(b["u0"]))
+        assert np.max(np.abs(a["grad"] - b["grad"])) <= 1e-10 * max(1.0, np.max(np.abs(b["grad"])))
+
+
+@pytest.mark.parametrize("which", ["nearest", "batch"])
+def test_subset_solves_equal_the_brute_force(which):
+    """K = 12 of M = 40: the selection, the weights normalised over the subset, the
+    regression and Newton per anchor, against the dense brute force (1e-10)."""
+    d, N, M, K = 3, 3, 40, 12
+    rng = np.random.default_rng(11)
+    x0 = rng.normal(scale=0.5, size=d)
+    p = _p("ac_manufactured", d, N, M, 2.0)
+    sel = _nearest(K) if which == "nearest" else _window(K, M)
+    ref_u, ref_g = _brute_force_anchored(p, x0, 3, 1, select=sel)
+    fn = oracle.solve_neighbours if which == "nearest" else oracle.solve_batch
+    r = fn(p, K, x0, 3, 1)
+    assert r["status"] == 0
+    assert abs(r["u0"] - ref_u) <= 1e-10 * max(1.0, abs(ref_u)), (r["u0"], ref_u)
+    assert np.max(np.abs(r["grad"] - ref_g)) <= 1e-9 * max(1.0, np.max(np.abs(ref_g)))
+
+
+def test_nearest_subset_is_biased_and_the_batch_is_not():
+    """Manufactured Allen-Cahn, d = 8, M = 800, N = 8, T = 0.5, x0 = 0 (u* = e^-T): the
+    regression over each anchor's 200 nearest particles misses u* by more than 0.2; a batch of
+    200 (the cyclic window) and all particles are within 0.01."""
+    d, N, M, K = 8, 8, 800, 200
+    p = _p("ac_manufactured", d, N, M, 2.0)
+    x0 = np.zeros(d)
+    exact = math.exp(-0.5)
+    near = oracle.solve_neighbours(p, K, x0, 3, 0)
+    batch = oracle.solve_batch(p, K, x0, 3, 0)
+    full = oracle.solve_anchored(p, x0, 3, 0)
+    assert near["status"] == batch["status"] == full["status"] == 0
+    assert abs(near["u0"] - exact) > 0.2
+    assert abs(batch["u0"] - exact) < 0.01 and abs(full["u0"] - exact) < 0.01
