@@ -216,6 +216,21 @@ FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const doub
                                    uint32_t solve_index0, double *u0, double *grad_u0,
                                    void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
 
+/* Algorithm 1 per particle anchor, each anchor's regression over a batch of K particles
+ * (the random-batch reading of Remark 2.1): for anchor m the batch is the cyclic window
+ * j = (m + q) mod M, q = 0..K-1.  The particle paths are independent and identically
+ * distributed and the window does not depend on them, so it is a random batch in law.  The
+ * Gaussian weights, the moments and the ridge are those of fbsde_solve_anchored restricted
+ * to the batch (weights normalised over it); K = M is fbsde_solve_anchored.
+ *   2 <= K <= M, else FBSDE_ERR_ARG; every other argument, the workspace
+ *   (fbsde_anchored_workspace_bytes), the blocking behaviour and the return codes are those
+ *   of fbsde_solve_anchored.  The contractions still run over all M particles (cost
+ *   O(M^2 d) per level and pass); the weights outside the window are zero.
+ */
+FBSDE_API int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
+                                uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
+                                void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
 /* Bytes of device workspace that fbsde_adjoint needs (the solve's workspace plus a tape
    of N (M + 2 d) values per query).  0 when the arguments are invalid. */
 FBSDE_API size_t fbsde_adjoint_workspace_bytes(const fbsde_problem *P, int32_t Q);

@@ -216,12 +216,14 @@ __global__ void __launch_bounds__(128) k_anc_rows(Params p, const Real *P, const
 // anchor m (thread per anchor); per-chunk partial sums go to part[chunk][m][.] and the
 // consumers add the chunks in order.
 //   mode 0: w_jm from rho_jm = pn_j + an_m - 2 G_jm, stored in W; sums w, w Y, w rho.
+//           With a batch of Kb < M particles per anchor (random-batch reading of Remark
+//           2.1), w_jm = 0 outside the cyclic window j = (m + q) mod M, q < Kb.
 //   mode 1: T_jm = w_jm (G_jm - A_m . v_m) / W_m stored in T; sum T.
 constexpr int kRowChunk = 64;
 template <typename Real>
-__global__ void k_anc_columns(Params p, int mode, double rho_ref, const Real *G, const double *pn,
-                              const double *an, const double *Y, Real *W, Real *T,
-                              const Anchor *st, double *part)
+__global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, const Real *G,
+                              const double *pn, const double *an, const double *Y, Real *W,
+                              Real *T, const Anchor *st, double *part)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
@@ -236,7 +238,9 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, const Real *G,
         const Real scale = p.uniform ? Real(0) : (Real)(-1.0 / (p.h2 * rho_ref));
         for (long long j = j0; j < j1; ++j) {
             const Real rho = max((Real)pn[j] + am - Real(2) * G[(size_t)j * p.M + m], Real(0));
-            const Real w = exp((rho - ref) * scale);
+            long long off = j - m;   // position of particle j in anchor m's window
+            if (off < 0) off += p.M;
+            const Real w = off < Kb ? exp((rho - ref) * scale) : Real(0);
             W[(size_t)j * p.M + m] = w;
             sw += w;
             swy += w * (Real)Y[j];
@@ -670,10 +674,11 @@ cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Re
 
 // One query: the forward sweep, then the levels k = N-1..0.  *status gets the first
 // device status (CG or Newton failure); the call synchronises on s for the CG checks.
+// Kb: particles per anchor's regression (the cyclic window; Kb = M: all of them).
 template <typename Real>
 cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
                       uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
-                      int *status, int *host_cnt)
+                      int *status, int *host_cnt, long long Kb)
 {
     cudaError_t e;
     Params p = params_of(Pb, L, seed);
@@ -709,7 +714,7 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         ANC_TRY(cudaGetLastError());
         ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, cnt + 1, s)));   // P A^T
         const double rho_ref = p.sigma * p.sigma * p.d * (t_k + (k + 1) * p.dt);
-        k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 0, rho_ref, G1, pn, an, Y, W, T, st, cs);
+        k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 0, rho_ref, Kb, G1, pn, an, Y, W, T, st, cs);
         ANC_TRY(cudaGetLastError());
         ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, cnt + 1, s)));    // W^T P
         ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, cnt + 1, s)));   // W^T (Y P)
@@ -725,7 +730,7 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
                                             TcColumnsEpi{W, T, st, cs, M}, cnt + 1, s)));
             } else {
                 ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, s)));   // U = P V^T
-                k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, G1, pn, an, Y, W, T, st, cs);
+                k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, Kb, G1, pn, an, Y, W, T, st, cs);
                 ANC_TRY(cudaGetLastError());
             }
             ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, s)));   // T^T P
@@ -769,8 +774,18 @@ int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, ui
                          uint32_t solve_index0, double *u0, double *grad_u0, void *workspace,
                          size_t workspace_bytes, fbsde_stream_t stream)
 {
+    return P ? fbsde_solve_batch(P, P->M, Q, x0, seed, solve_index0, u0, grad_u0, workspace,
+                                 workspace_bytes, stream)
+             : FBSDE_ERR_ARG;
+}
+
+int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
+                      uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
+                      void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
+{
     Lay L;
     if (!lay(P, L) || Q < 1 || !x0 || !u0) return FBSDE_ERR_ARG;
+    if (K < 2 || K > L.M) return FBSDE_ERR_ARG;
     if ((P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) && !P->theta)
         return FBSDE_ERR_ARG;
     if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAl))
@@ -784,9 +799,9 @@ int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, ui
         const cudaError_t e =
             P->precision == FBSDE_FP32
                 ? solve_one<float>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, &status,
-                                   &host_cnt)
+                                   &host_cnt, K)
                 : solve_one<double>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, &status,
-                                    &host_cnt);
+                                    &host_cnt, K);
         if (e != cudaSuccess) return FBSDE_ERR_CUDA;
     }
     return status;

@@ -72,7 +72,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
-           "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored"]
+           "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 12
 FBSDE_MAX_D = 16384
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_anchored_workspace_bytes.restype = SZ
         lib.fbsde_solve_anchored.argtypes = [P, I32, V, U64, U32, V, V, V, SZ, V]
         lib.fbsde_solve_anchored.restype = C.c_int
+        lib.fbsde_solve_batch.argtypes = [P, C.c_int64, I32, V, U64, U32, V, V, V, SZ, V]
+        lib.fbsde_solve_batch.restype = C.c_int
         lib.fbsde_adjoint_workspace_bytes.argtypes = [P, I32]
         lib.fbsde_adjoint_workspace_bytes.restype = SZ
         lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
@@ -231,8 +233,19 @@ def fbsde_solve_anchored(problem: fbsde_problem, Q: int, x0, seed: int, solve_in
         _stream(stream)))
 
 
-def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0) -> dict:
-    """Per-anchor solve of the CUDA tensor x0 [Q, d]; returns u0 [Q], grad [Q, d], status."""
+def fbsde_solve_batch(problem: fbsde_problem, K: int, Q: int, x0, seed: int, solve_index0: int,
+                      u0, grad_u0, workspace, stream=None) -> int:
+    """Algorithm 1 per anchor over a batch of K particles (cyclic window; blocking call)."""
+    return int(load_library().fbsde_solve_batch(
+        C.byref(problem), int(K), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream)))
+
+
+def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0,
+                   K: int | None = None) -> dict:
+    """Per-anchor solve of the CUDA tensor x0 [Q, d]; returns u0 [Q], grad [Q, d], status.
+    With K, each anchor's regression runs over its batch of K particles (fbsde_solve_batch)."""
     import torch
     Q = x0.shape[0]
     nbytes = fbsde_anchored_workspace_bytes(problem)
@@ -241,9 +254,12 @@ def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=x0.device)
     u = torch.empty(Q, dtype=torch.float64, device=x0.device)
     g = torch.empty(Q, problem.d, dtype=torch.float64, device=x0.device)
-    st = fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws)
+    if K is None:
+        st, name = fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws), "fbsde_solve_anchored"
+    else:
+        st, name = fbsde_solve_batch(problem, K, Q, x0, seed, solve_index0, u, g, ws), "fbsde_solve_batch"
     if st not in (FBSDE_OK, FBSDE_ERR_CG, FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE):
-        check(st, "fbsde_solve_anchored")
+        check(st, name)
     return {"u0": u, "grad": g, "status": st}
 
 

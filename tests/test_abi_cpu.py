@@ -184,3 +184,14 @@ def test_plan_workspace_is_the_aligned_sum_of_the_instances(lib):
     assert lib.fbsde_plan_create(C.byref(h), 1, arr, 0, None, 0) == 2
     assert lib.fbsde_plan_create(C.byref(h), 1, arr, 0, C.c_void_p(fake), up(a) - 1) == 2
     assert h.value is None
+
+
+def test_batch_argument_errors_return_synchronously(lib):
+    p = _prob(M=256)
+    n = fbsde.fbsde_anchored_workspace_bytes(p)
+    fake = C.c_void_p(1 << 20)
+    for K in (1, 0, 257, -5):
+        assert lib.fbsde_solve_batch(C.byref(p), K, 1, fake, 0, 0, fake, None, fake, n, None) == 1
+    assert lib.fbsde_solve_batch(C.byref(p), 64, 1, None, 0, 0, fake, None, fake, n, None) == 1
+    assert lib.fbsde_solve_batch(C.byref(p), 64, 1, fake, 0, 0, fake, None, fake, n - 1, None) == 2
+    assert lib.fbsde_solve_batch(None, 64, 1, fake, 0, 0, fake, None, fake, n, None) == 1

@@ -1,6 +1,7 @@
 """Algorithm 1 with one regression per particle anchor: the CUDA path against the oracle's
 literal per-anchor solve on the same seeds (FP64 within 1e-10, FP32 within 1e-4), and, with
-uniform weights, against the single-anchor entry point.  Sizes are ragged with respect to
+uniform weights, against the single-anchor entry point; the same for each anchor's
+regression over a batch of K particles (fbsde_solve_batch against the oracle's subset loop).  Sizes are ragged with respect to
 the 64 x 64 tiles of the SIMT contractions, the 128 x 128 tiles of the tensor-core ones
 (M >= 1024, FP32) and the 16-byte row chunks."""
 import math
@@ -24,7 +25,7 @@ CASES = [
 ]
 
 
-def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13):
+def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13, K=None):
     extra = dict(extra)
     sigma, T, h = extra.pop("sigma", 1.0), extra.pop("T", 0.5), extra.pop("h", 2.0)
     rng = np.random.default_rng(d * 1000 + M)
@@ -34,11 +35,14 @@ def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13):
     th_dev = torch.tensor(theta, device="cuda") if theta is not None else None
     p = fb.make_problem(kind, d, N, M, sigma, T, prec, theta=th_dev, h=h, cg_tol=tol,
                         cg_max_iter=1000, **extra)
-    out = fb.solve_anchored(p, torch.tensor(x0, device="cuda"), seed, 0)
+    out = fb.solve_anchored(p, torch.tensor(x0, device="cuda"), seed, 0, K=K)
     torch.cuda.synchronize()
     op = oracle.Problem(kind, d, sigma, T, N, M, theta=theta, h=h, cg_tol=1e-13,
                         cg_max_iter=1000, **extra)
-    refs = [oracle.solve_anchored(op, x0[q], seed, q) for q in range(Q)]
+    if K is None:
+        refs = [oracle.solve_anchored(op, x0[q], seed, q) for q in range(Q)]
+    else:
+        refs = [oracle.solve_batch(op, K, x0[q], seed, q) for q in range(Q)]
     return out, refs, p, x0, th_dev
 
 
@@ -109,3 +113,38 @@ def test_argument_errors():
     x0 = torch.zeros(1, 10, dtype=torch.float64, device="cuda")
     u = torch.empty(1, dtype=torch.float64, device="cuda")
     assert fb.fbsde_solve_anchored(p, 1, x0, 0, 0, u, None, ws) == fb.FBSDE_ERR_ARG
+
+
+# Drivers whose Newton derivative stays away from 0 on small batches (a gradient-dependent
+# driver with a large sigma makes F' = 1 - dt sum_i z_i, built from a few noisy slopes, pass
+# near 0, where both sides' Newton iterations are at the mercy of rounding).
+BATCH_CASES = [
+    ("ac_manufactured", 10, 150, 3, 40, {}),
+    ("cos_linear_test", 5, 97, 3, 31, {"c1": 0.4}),
+    ("hjb_logquad", 9, 130, 3, 64, {"sigma": math.sqrt(2.0), "T": 1.0, "theta": True}),
+    ("ac_doublewell", 16, 65, 3, 33, {"sigma": math.sqrt(2.0), "T": 0.3}),
+]
+
+
+@pytest.mark.parametrize("kind,d,M,N,K,extra", BATCH_CASES)
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32", TOL_FP32)])
+def test_batch_matches_oracle(kind, d, M, N, K, extra, prec, tol):
+    """Each anchor's regression over its batch of K particles (the cyclic window, the
+    random-batch reading of Remark 2.1) against the oracle's literal subset loop."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, kind, d, M, N, prec, extra, K=K)
+    _check(out, refs, tol)
+
+
+def test_smallest_batch_fp64_matches_oracle():
+    """K = 2 < d: each anchor's regression is underdetermined and held by the ridge."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, "ac_doublewell", 16, 65, 3, "fp64",
+                         {"sigma": math.sqrt(2.0), "T": 0.3}, K=2)
+    _check(out, refs, TOL_FP64)
+
+
+def test_batch_on_the_tensor_core_path_matches_oracle():
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, "ac_manufactured", 21, 1030, 2, "fp32", {}, Q=1, K=300)
+    _check(out, refs, TOL_FP32)
