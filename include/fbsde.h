@@ -131,7 +131,8 @@ typedef struct {
     int32_t cg_iters_total;  /* CG iterations over all levels and queries of the solve    */
 } fbsde_diag;
 
-/* Bytes of device workspace that fbsde_solve needs for Q query points of problem P.
+/* Bytes of device workspace that fbsde_solve needs for Q query points of problem P (the
+   particle rows, weights and regression vectors of Algorithm 1, laid out per query).
    Returns 0 when the arguments are invalid. */
 FBSDE_API size_t fbsde_workspace_bytes(const fbsde_problem *P, int32_t Q);
 
@@ -156,7 +157,7 @@ FBSDE_API int fbsde_solve(const fbsde_problem *P, int32_t Q, const double *x0, u
                 void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
 
 /*
- * The same solve with the query points and results in HOST memory: copies x0 to
+ * Algorithm 1 as fbsde_solve, with the query points and results in HOST memory: copies x0 to
  * the device, solves, copies u0 and grad_u0 back and synchronises the stream.
  * theta (if the kind needs it) is read from P->theta as a HOST pointer here.
  * grad_u0 may be NULL.  Returns the solve's device status as well (blocking call).
@@ -256,11 +257,13 @@ FBSDE_API int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0,
                             double *grad_u0, double *x0_bar, double *theta_bar, void *workspace,
                             size_t workspace_bytes, fbsde_stream_t stream);
 
-/* Extra workspace bytes fbsde_solve_host needs on top of fbsde_workspace_bytes. */
+/* Extra workspace bytes fbsde_solve_host needs on top of fbsde_workspace_bytes (device
+   staging of x0, u0 and grad u0; no counterpart in the paper). */
 FBSDE_API size_t fbsde_host_staging_bytes(const fbsde_problem *P, int32_t Q);
 
 /* Synchronises the stream and reads the device-side status of the last solve that
-   used this workspace. */
+   used this workspace: CG exhaustion of the regression solves (Eqs. 3.19-3.20), the
+   largest Newton iteration count (Eqs. 2.16-2.17), non-finite results, timeouts. */
 FBSDE_API int fbsde_diagnostics(const fbsde_problem *P, int32_t Q, const void *workspace,
                       fbsde_diag *out, fbsde_stream_t stream);
 
@@ -277,8 +280,9 @@ FBSDE_API int fbsde_normals(uint64_t seed, uint32_t s, uint32_t k, uint32_t j0, 
                   int32_t precision, void *out, fbsde_stream_t stream);
 
 /*
- * Plans: a solve, or a batch of heterogeneous solves, captured once into a CUDA graph
- * and replayed with one launch.  Each CG loop is a conditional while node whose body
+ * Plans: a solve, or a batch of heterogeneous solves (each Algorithm 1 on its own problem,
+ * query points and cloud; the batching itself has no counterpart in the paper), captured
+ * once into a CUDA graph and replayed with one launch.  Each CG loop is a conditional while node whose body
  * (product, reduction, CG step, convergence check) repeats on the device until every
  * query of that instance has converged, so no empty iterations are launched.  Instances
  * are spread over parallel graph branches and run concurrently on the GPU.  The
@@ -337,8 +341,8 @@ typedef struct {
     double total_ms;   /* summed event time of the timed launches                     */
 } fbsde_kernel_stats;
 
-/* Process-wide launch profiler (off by default; not for concurrent solves from several
-   host threads).  After fbsde_profile_start(n), every launch is counted and the first
+/* Process-wide launch profiler (measurement of the kernels above; no counterpart in the
+   paper; off by default; not for concurrent solves from several host threads).  After fbsde_profile_start(n), every launch is counted and the first
    n launches are bracketed by CUDA events recorded on the launching stream.
    fbsde_profile_stop() waits for the recorded events, fills out[FBSDE_NUM_KERNELS]
    and switches the profiler off.  fbsde_profile_select(mask) restricts the timing to
@@ -360,8 +364,11 @@ typedef struct {
 FBSDE_API int fbsde_profile_start(int32_t max_timed_launches);
 FBSDE_API int fbsde_profile_select(uint32_t family_mask);
 FBSDE_API int fbsde_profile_stop(fbsde_kernel_stats *out);
+/* Name of a kernel family ("matvec", ...); "unknown" outside the enum. */
 FBSDE_API const char *fbsde_kernel_name(int family);
 
+/* Utilities without a counterpart in the paper: a static description of a status code
+   (never NULL), and FBSDE_ABI_VERSION of the loaded library. */
 FBSDE_API const char *fbsde_status_string(int status);
 FBSDE_API int fbsde_abi_version(void);
 
