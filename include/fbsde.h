@@ -332,7 +332,10 @@ typedef enum {
     FBSDE_K_PARTICLES = 9,  /* per-particle terminal value / prediction + Newton, weights*/
     FBSDE_K_FINALIZE = 10,  /* per-query regression set-up from the moments              */
     FBSDE_K_ADJOINT = 11,   /* reverse-sweep kernels other than the shared ones above    */
-    FBSDE_NUM_KERNELS = 12
+    FBSDE_K_STEP = 12,      /* fused level step of the FP32 path (d <= 10240): reverse step
+                               of the rows, Newton (2.16)-(2.17), weights and moments in
+                               one pass; the forward sweep's end point at k = N          */
+    FBSDE_NUM_KERNELS = 13
 } fbsde_kernel_family;
 
 typedef struct {

@@ -92,6 +92,36 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
                     (size_t)L.teams * 2 * 32 * L.real_sz;
         if (L.mv_smem > 227 * 1024) return FBSDE_ERR_ARG;
     }
+    // fused per-level step (FP32 rows up to kStepMaxLd floats): R rows per stage, the
+    // largest of {1, 3, 5, 15, 30} with R ld <= kStepElems (at most 30: one scalar-warp lane
+    // per row), T = 480 / R threads per row in the row pass (whole warps, or half-warps at
+    // R = 30), VM = ceil(nch / T) chunks per thread; column pass in row groups of
+    // tpr = min(480, nch) threads; two row slots when R = 1 (row and column passes then own
+    // the same chunks), three otherwise
+    L.fused = P->precision == FBSDE_FP32 && L.ld <= kStepMaxLd;
+    if (L.fused) {
+        constexpr int kRows[5] = {1, 3, 5, 15, 30};
+        int R = 1;
+        for (int r : kRows)
+            if ((size_t)r * L.ld <= (size_t)kStepElems) R = r;
+        L.st_R = R;
+        L.st_T = 480 / R;
+        L.st_vm1 = (nch + L.st_T - 1) / L.st_T;
+        L.st_tpr = std::min(480, nch);
+        L.st_RG = 480 / L.st_tpr;
+        L.st_vm3 = (nch + L.st_tpr - 1) / L.st_tpr;
+        L.st_vm = L.st_vm1;
+        L.st_nslot = R == 1 ? 2 : 3;
+        const size_t slots = (size_t)L.st_nslot * R * L.ld;
+        const size_t red = L.st_RG > 1 ? (size_t)L.st_RG * 3 * nch * 4 : 0;
+        L.st_region = std::max(slots, red);
+        const size_t tail = L.st_vm3 > 5 ? (size_t)3 * (nch - 5 * 480) * 16 : 0;
+        L.st_smem = (3 * (size_t)L.ld + L.st_region) * sizeof(float) + 4 * 32 * 16 + tail;
+        if (L.st_vm > 6 || L.st_vm3 > L.st_vm || (L.st_vm3 > 5 && R != 1) ||
+            L.st_smem > 227 * 1024)
+            return FBSDE_ERR_ARG;
+    }
+    L.GS = std::max(L.GP, L.fused ? L.G : 0);
     // partial reduction: tiles of kRedTile elements, red_groups warps per tile, each adding
     // about four of the G partials
     L.nblk = (L.ld + kRedTile - 1) / kRedTile;
@@ -112,7 +142,7 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_coef = take(Qs * Ms * 3 * L.real_sz);
     L.off_segp = take(Qs * Ms * (size_t)L.nseg * kSegSums * L.real_sz);
     L.off_part = take(Qs * L.G * kPartVecs * lds * L.real_sz);
-    L.off_spart = take(Qs * L.GP * kPartScal * sizeof(double));
+    L.off_spart = take(Qs * L.GS * kPartScal * sizeof(double));
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
@@ -140,7 +170,16 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.Q = L.Q;
     p.nseg = L.nseg;
     p.GP = L.GP;
-    p.GS = L.GP;
+    p.GS = L.GS;
+    p.nsp = L.fused ? L.G : L.GP;
+    p.st_R = L.st_R;
+    p.st_T = L.st_T;
+    p.st_vm1 = L.st_vm1;
+    p.st_tpr = L.st_tpr;
+    p.st_RG = L.st_RG;
+    p.st_vm3 = L.st_vm3;
+    p.st_nslot = L.st_nslot;
+    p.st_region = (long long)L.st_region;
     p.mv_rows = L.mv_rows;
     p.mv_stages = L.mv_stages;
     p.team_warps = L.team_warps;
@@ -417,11 +456,15 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
     cudaError_t e;
     const cudaStream_t s = r.s;
     FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, s));
-    FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
     p.level = p.N;
-    FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+    if (L.fused) {   // forward sweep end point, g and the first regression's moments in one pass
+        FBSDE_TRY(FBSDE_K_STEP, LR::step(p, L, s));
+    } else {
+        FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
+        FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+    }
     if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
-    FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+    if (!L.fused) FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
     FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
     p.newton_level = -1;
     FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 0, s));
@@ -430,9 +473,13 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
         if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
         FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
         if (k >= 1) {
-            FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
-            FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
-            FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+            if (L.fused) {   // the whole level step in one pass over the rows
+                FBSDE_TRY(FBSDE_K_STEP, LR::step(p, L, s));
+            } else {
+                FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
+                FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+                FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+            }
             FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
             p.newton_level = k;
             FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
@@ -938,7 +985,7 @@ const char *fbsde_kernel_name(int family)
 {
     static const char *names[FBSDE_NUM_KERNELS] = {
         "setup", "forward", "update", "matvec", "moments", "reduce",
-        "cg_step", "cg_post", "trace", "particles", "finalize", "adjoint"};
+        "cg_step", "cg_post", "trace", "particles", "finalize", "adjoint", "step"};
     return (family >= 0 && family < FBSDE_NUM_KERNELS) ? names[family] : "unknown";
 }
 

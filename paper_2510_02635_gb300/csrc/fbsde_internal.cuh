@@ -41,6 +41,8 @@ constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
 constexpr int kMinRowsPerCta = 8;
 constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-stride)
+constexpr int kStepMaxLd = 10240;    // widest FP32 row of the fused per-level step
+constexpr int kStepElems = 10240;    // particle-dims per stage of the fused step
 
 struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
@@ -57,6 +59,10 @@ struct Layout {
     size_t off_tape_w, off_tape_Y, off_tape_v, off_tape_s, off_adj_v, total_adjoint;
     int seg_vpt, nseg, GP, mom_vm, mom_tiles, row_blocks, mv_rows, mv_stages, red_groups, nblk;
     size_t mv_smem;
+    // fused per-level step (FP32 rows of at most kStepMaxLd floats): rows per stage, threads
+    // per row, chunks per thread in the row pass, column-pass row groups, shared memory
+    int fused, st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_vm, st_nslot, GS;
+    size_t st_region, st_smem;
     int64_t M;
     size_t real_sz;
     size_t off_delta, off_Y, off_w, off_coef, off_segp, off_part, off_spart, off_vec64, off_vecR,
@@ -72,6 +78,9 @@ struct Params {
     long long M;
     double sigma, T, dt, sdt, A, c0, c1, c2, c3, h2, ridge_rel, cg_tol2, newton_tol;
     double wa, wb;  // path step of the row kernels: Delta <- wa Delta + wb xi (set per launch)
+    int st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_nslot, nsp;  // fused step geometry;
+                                                                    // nsp = spart blocks of a level
+    long long st_region;  // floats of the fused step's row-slot region
     uint32_t key0, key1, solve0;
     // workspace
     void *delta;
@@ -102,6 +111,7 @@ template <typename Real> struct Launch {
     static cudaError_t update(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t particles(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t moments(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t step(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t reduce(const Params &p, const Layout &L, int nvec, int dst0, int skip_done,
                               cudaStream_t s);
     static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);

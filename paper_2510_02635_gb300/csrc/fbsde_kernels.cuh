@@ -44,10 +44,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// 32-bit word -> ((x >> 9) + 1/2) 2^-23 in (0,1), exact in binary32.
+// 32-bit word -> ((x >> 9) + 1/2) 2^-23 in (0,1), exact in binary32: the funnel shift puts
+// the top 23 bits of x under the exponent bits of 1.0 (0x7F << 23), giving
+// 1 + (x >> 9) 2^-23 in [1, 2); subtracting 1 - 2^-24 is exact, since the result
+// (2 (x >> 9) + 1) 2^-24 has at most 24 significant bits.
 __device__ __forceinline__ float u01f(uint32_t x)
 {
-    return (__uint2float_rn(x >> 9) + 0.5f) * 0x1p-23f;
+    return __uint_as_float(__funnelshift_r(x, 0x7Fu, 9)) - (1.0f - 0x1p-24f);
 }
 __device__ __forceinline__ double u01d(uint32_t x)
 {
@@ -71,41 +74,28 @@ __device__ __forceinline__ float ln_unit(float u)
     return u > 0.75f ? near1 : __logf(u);
 }
 
-// (sin, cos)(2 pi u) for u in (0, 1) in FP32: n = rint(4u) quarter turns, remainder
-// f = 4u - n in [-1/2, 1/2] (exact), angle f pi/2 in [-pi/4, pi/4], Taylor polynomials
-// of degree 9 (sin) and 8 (cos) there (truncation below 3e-8), then the rotation by n
-// quarter turns.
-__device__ __forceinline__ void sincos_turn(float u, float &sn, float &cs)
-{
-    const float t = 4.0f * u;
-    const float n = rintf(t);
-    const float th = (t - n) * 1.57079632679489662f;
-    const float t2 = th * th;
-    float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-    ps = fmaf(t2, ps, 1.0f / 120.0f);
-    ps = fmaf(t2, ps, -1.0f / 6.0f);
-    const float s0 = fmaf(th * t2, ps, th);
-    float pc = fmaf(t2, 1.0f / 40320.0f, -1.0f / 720.0f);
-    pc = fmaf(t2, pc, 1.0f / 24.0f);
-    pc = fmaf(t2, pc, -0.5f);
-    const float c0 = fmaf(t2, pc, 1.0f);
-    const int q = ((int)n) & 3;
-    const float sx = (q & 1) ? c0 : s0, cx = (q & 1) ? s0 : c0;
-    sn = (q & 2) ? -sx : sx;
-    cs = ((q + 1) & 2) ? -cx : cx;
-}
-
-// Box-Muller (1958): (a, b) -> sqrt(-2 ln u_a) (cos, sin)(2 pi u_b).  FP32: ln_unit,
-// sqrt(L) as L / sqrt(L) with the hardware reciprocal square root, sincos_turn; the
-// normals stay within 2e-7 of the FP64 transform of the same words (measured on 4M).
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+// Box-Muller (1958): (a, b) -> sqrt(-2 ln u_a) (cos, sin)(2 pi u_b), times `scale`.
+// FP32: ln_unit; sqrt(L) as L / sqrt(L) with the hardware reciprocal square root; the angle
+// taken as theta = 2 pi u_b - pi in (-pi, pi), where the hardware sine and cosine are
+// accurate to 3.4e-7 absolute (measured on every u_b of the 2^23-point grid), and
+// (cos, sin)(2 pi u_b) = -(cos, sin)(theta), the sign folded into the radius.  The normals
+// stay within 2e-6 of the FP64 transform of the same words.  The scale (the path
+// step's sigma sqrt(dt) factor) multiplies the radius once per pair; scale = 1 gives the
+// normals themselves.
+__device__ __forceinline__ void box_muller_scaled(uint32_t a, uint32_t b, float scale, float &z0,
+                                                  float &z1)
 {
     const float L = -2.0f * ln_unit(u01f(a));
-    const float r = L * rsqrtf(L);
+    const float nr = -scale * (L * rsqrtf(L));
+    const float th = fmaf(u01f(b), 6.28318530717958648f, -3.14159265358979324f);
     float sn, cs;
-    sincos_turn(u01f(b), sn, cs);
-    z0 = r * cs;
-    z1 = r * sn;
+    __sincosf(th, &sn, &cs);
+    z0 = nr * cs;
+    z1 = nr * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    box_muller_scaled(a, b, 1.0f, z0, z1);
 }
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &z0, double &z1)
 {
@@ -1036,7 +1026,7 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     const WS<Real> ws(p);
     SolveState &st = p.st[s];
     double W = 0.0, Cp = 0.0, Rr = 0.0;
-    for (int b = 0; b < p.GP; ++b) {
+    for (int b = 0; b < p.nsp; ++b) {
         const double *sp = ws.spart(s, b);
         W += sp[0];
         Cp += sp[1];

@@ -3,6 +3,7 @@
 #include "fbsde_adjoint.cuh"
 #include "fbsde_kernels.cuh"
 #include "fbsde_matvec.cuh"
+#include "fbsde_step.cuh"
 
 namespace fbsde {
 
@@ -76,6 +77,55 @@ cudaError_t Launch<Real>::moments(const Params &p, const Layout &L, cudaStream_t
         dev::k_moments<Real, 2><<<grid, 256, smem, s>>>(p);
     }
     return cudaGetLastError();
+}
+
+// Fused per-level step (FP32 rows of at most kStepMaxLd floats): level k = p.level, with
+// 1 <= k < N the Brownian-bridge step Delta_k = a Delta_{k+1} + b xi_k (a = k/(k+1),
+// b = sigma sqrt(dt k/(k+1)), as in update), and k = N the end point
+// Delta_N = sigma sqrt(T) xi_N of the forward sweep.
+template <int VM, bool COSF, bool TERM>
+static cudaError_t launch_step(const Params &q, const Layout &L, cudaStream_t s)
+{
+    cudaError_t e = set_smem(dev::k_step<VM, COSF, TERM>, L.st_smem);
+    if (e != cudaSuccess) return e;
+    dev::k_step<VM, COSF, TERM><<<dim3(L.G, L.Q), dev::kStepThreads, L.st_smem, s>>>(q);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::step(const Params &p, const Layout &L, cudaStream_t s)
+{
+    if constexpr (sizeof(Real) != sizeof(float)) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (!L.fused || p.level < 1 || p.level > p.N) return cudaErrorInvalidValue;
+        Params q = p;
+        if (p.level == p.N) {
+            q.wa = 0.0;
+            q.wb = p.sigma * std::sqrt(p.T);
+        } else {
+            const double a = (double)p.level / (double)(p.level + 1);
+            q.wa = a;
+            q.wb = p.sigma * std::sqrt(p.dt * a);
+        }
+        const bool term = p.level == p.N;
+        const bool cosf = !term && p.kind == FBSDE_AC_MANUFACTURED;
+#define FBSDE_STEP_CASE(VM)                                                              \
+    case VM:                                                                             \
+        return term ? launch_step<VM, false, true>(q, L, s)                              \
+                    : (cosf ? launch_step<VM, true, false>(q, L, s)                      \
+                            : launch_step<VM, false, false>(q, L, s));
+        switch (L.st_vm) {
+            FBSDE_STEP_CASE(1)
+            FBSDE_STEP_CASE(2)
+            FBSDE_STEP_CASE(3)
+            FBSDE_STEP_CASE(4)
+            FBSDE_STEP_CASE(5)
+            FBSDE_STEP_CASE(6)
+        }
+#undef FBSDE_STEP_CASE
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename Real>

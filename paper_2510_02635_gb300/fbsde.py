@@ -74,7 +74,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
            "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
-FBSDE_NUM_KERNELS = 12
+FBSDE_NUM_KERNELS = 13
 FBSDE_MAX_D = 16384
 FBSDE_MAX_D_FP64 = 8192
 FBSDE_PROFILED_EAGER_PASSES = 48   # the header constant of the same name
