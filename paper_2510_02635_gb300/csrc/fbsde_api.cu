@@ -93,11 +93,10 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
         if (L.mv_smem > 227 * 1024) return FBSDE_ERR_ARG;
     }
     // fused per-level step (FP32 rows up to kStepMaxLd floats): R rows per stage, the
-    // largest of {1, 3, 5, 15, 30} with R ld <= kStepElems (at most 30: one scalar-warp lane
+    // largest of {1, 3, 5, 15, 30} with R ld <= kStepElems (at most 30: one service-warp lane
     // per row), T = 480 / R threads per row in the row pass (whole warps, or half-warps at
     // R = 30), VM = ceil(nch / T) chunks per thread; column pass in row groups of
-    // tpr = min(480, nch) threads; two row slots when R = 1 (row and column passes then own
-    // the same chunks), three otherwise
+    // tpr = min(480, nch) threads; a two-slot ring of stages in shared memory
     L.fused = P->precision == FBSDE_FP32 && L.ld <= kStepMaxLd;
     if (L.fused) {
         constexpr int kRows[5] = {1, 3, 5, 15, 30};
@@ -111,12 +110,12 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
         L.st_RG = 480 / L.st_tpr;
         L.st_vm3 = (nch + L.st_tpr - 1) / L.st_tpr;
         L.st_vm = L.st_vm1;
-        L.st_nslot = R == 1 ? 2 : 3;
-        const size_t slots = (size_t)L.st_nslot * R * L.ld;
+        L.st_nslot = 2;
+        const size_t ring = (size_t)2 * R * L.ld;
         const size_t red = L.st_RG > 1 ? (size_t)L.st_RG * 3 * nch * 4 : 0;
-        L.st_region = std::max(slots, red);
+        L.st_region = std::max(ring, red);
         const size_t tail = L.st_vm3 > 5 ? (size_t)3 * (nch - 5 * 480) * 16 : 0;
-        L.st_smem = (3 * (size_t)L.ld + L.st_region) * sizeof(float) + 4 * 32 * 16 + tail;
+        L.st_smem = (3 * (size_t)L.ld + L.st_region) * sizeof(float) + 4 * 32 * 16 + 48 + tail;
         if (L.st_vm > 6 || L.st_vm3 > L.st_vm || (L.st_vm3 > 5 && R != 1) ||
             L.st_smem > 227 * 1024)
             return FBSDE_ERR_ARG;
@@ -204,6 +203,10 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.theta = P->theta;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {   // Weyl sequence of the Philox key, one entry per round
+        p.rk0[r] = p.key0 + (uint32_t)r * 0x9E3779B9u;
+        p.rk1[r] = p.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     p.solve0 = solve0;
     char *base = static_cast<char *>(ws);
     p.delta = base + L.off_delta;

@@ -81,6 +81,7 @@ struct Params {
     int st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_nslot, nsp;  // fused step geometry;
                                                                     // nsp = spart blocks of a level
     long long st_region;  // floats of the fused step's row-slot region
+    uint32_t rk0[10], rk1[10];  // Philox4x32-10 round keys of (key0, key1)
     uint32_t key0, key1, solve0;
     // workspace
     void *delta;

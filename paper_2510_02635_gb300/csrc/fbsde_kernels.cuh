@@ -37,11 +37,64 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // the two 32 x 32 -> 64-bit products, high and low halves from one multiply each
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     }
     return c;
+}
+
+// The same generator with the ten round keys precomputed (rk0[r] = k0 + r W0,
+// rk1[r] = k1 + r W1), read from the kernel's parameter space.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk0,
+                                                  const uint32_t *rk1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[round], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[round], (uint32_t)p0);
+    }
+    return c;
+}
+
+// Hardware approximations of the special-function unit with denormal inputs and results
+// flushed to zero (every argument they get here is a normal number: u >= 2^-24, L >= 1e-7,
+// angles and coordinates of order one), so no denormal range fix-up is compiled around
+// them: base-2 logarithm, reciprocal, reciprocal square root, sine and cosine of an angle
+// in radians.
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_ftz(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_ftz(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // 32-bit word -> ((x >> 9) + 1/2) 2^-23 in (0,1), exact in binary32: the funnel shift puts
@@ -57,21 +110,21 @@ __device__ __forceinline__ double u01d(uint32_t x)
     return ((double)(x >> 9) + 0.5) * 0x1p-23;
 }
 
-// ln u for u in (0, 1) in FP32.  For u <= 3/4 the hardware logarithm, whose error is
-// small relative to |ln u| >= 0.287 there; above, where ln u -> 0 and an absolute error
-// would dominate, the series ln u = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9),
-// s = (u - 1)/(u + 1) in [-1/7, 0) (u - 1 is exact; the next term is below 2e-9
-// relative).  Both are evaluated and one selected, so the warp does not diverge.
+// ln u for u in (0, 1) in FP32.  For u <= 3/4 the hardware base-2 logarithm times ln 2,
+// whose error is small relative to |ln u| >= 0.287 there; above, where ln u -> 0 and an
+// absolute error would dominate, the series ln u = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 +
+// s^7/7 + s^9/9), s = (u - 1)/(u + 1) in [-1/7, 0) (u - 1 is exact; the next term is below
+// 2e-9 relative).  Both are evaluated and one selected, so the warp does not diverge.
 __device__ __forceinline__ float ln_unit(float u)
 {
-    const float s = __fdividef(u - 1.0f, u + 1.0f);
+    const float s = (u - 1.0f) * rcp_ftz(u + 1.0f);
     const float s2 = s * s;
     float p = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
     p = fmaf(s2, p, 0.2f);
     p = fmaf(s2, p, 1.0f / 3.0f);
     p = fmaf(s2, p, 1.0f);
     const float near1 = 2.0f * s * p;
-    return u > 0.75f ? near1 : __logf(u);
+    return u > 0.75f ? near1 : lg2_ftz(u) * 0.693147180559945309f;
 }
 
 // Box-Muller (1958): (a, b) -> sqrt(-2 ln u_a) (cos, sin)(2 pi u_b), times `scale`.
@@ -86,12 +139,10 @@ __device__ __forceinline__ void box_muller_scaled(uint32_t a, uint32_t b, float 
                                                   float &z1)
 {
     const float L = -2.0f * ln_unit(u01f(a));
-    const float nr = -scale * (L * rsqrtf(L));
+    const float nr = -scale * (L * rsqrt_ftz(L));
     const float th = fmaf(u01f(b), 6.28318530717958648f, -3.14159265358979324f);
-    float sn, cs;
-    __sincosf(th, &sn, &cs);
-    z0 = nr * cs;
-    z1 = nr * sn;
+    z0 = nr * cos_ftz(th);
+    z1 = nr * sin_ftz(th);
 }
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
 {

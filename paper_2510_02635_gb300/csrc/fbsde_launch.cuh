@@ -83,13 +83,22 @@ cudaError_t Launch<Real>::moments(const Params &p, const Layout &L, cudaStream_t
 // 1 <= k < N the Brownian-bridge step Delta_k = a Delta_{k+1} + b xi_k (a = k/(k+1),
 // b = sigma sqrt(dt k/(k+1)), as in update), and k = N the end point
 // Delta_N = sigma sqrt(T) xi_N of the forward sweep.
-template <int VM, bool COSF, bool TERM>
+template <int VM, bool COSF, bool TERM, bool ONE>
 static cudaError_t launch_step(const Params &q, const Layout &L, cudaStream_t s)
 {
-    cudaError_t e = set_smem(dev::k_step<VM, COSF, TERM>, L.st_smem);
+    cudaError_t e = set_smem(dev::k_step<VM, COSF, TERM, ONE>, L.st_smem);
     if (e != cudaSuccess) return e;
-    dev::k_step<VM, COSF, TERM><<<dim3(L.G, L.Q), dev::kStepThreads, L.st_smem, s>>>(q);
+    dev::k_step<VM, COSF, TERM, ONE><<<dim3(L.G, L.Q), dev::kStepThreads, L.st_smem, s>>>(q);
     return cudaGetLastError();
+}
+
+template <int VM, bool ONE>
+static cudaError_t launch_step_kind(const Params &q, const Layout &L, bool term, bool cosf,
+                                    cudaStream_t s)
+{
+    if (term) return launch_step<VM, false, true, ONE>(q, L, s);
+    return cosf ? launch_step<VM, true, false, ONE>(q, L, s)
+                : launch_step<VM, false, false, ONE>(q, L, s);
 }
 
 template <typename Real>
@@ -112,9 +121,8 @@ cudaError_t Launch<Real>::step(const Params &p, const Layout &L, cudaStream_t s)
         const bool cosf = !term && p.kind == FBSDE_AC_MANUFACTURED;
 #define FBSDE_STEP_CASE(VM)                                                              \
     case VM:                                                                             \
-        return term ? launch_step<VM, false, true>(q, L, s)                              \
-                    : (cosf ? launch_step<VM, true, false>(q, L, s)                      \
-                            : launch_step<VM, false, false>(q, L, s));
+        return L.st_R == 1 ? launch_step_kind<VM, true>(q, L, term, cosf, s)             \
+                           : launch_step_kind<VM, false>(q, L, term, cosf, s);
         switch (L.st_vm) {
             FBSDE_STEP_CASE(1)
             FBSDE_STEP_CASE(2)

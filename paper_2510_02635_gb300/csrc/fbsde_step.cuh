@@ -8,28 +8,32 @@
 // (k = N) runs the same kernel without the read: the forward sweep's end point, g and the
 // first regression's moments.  Included after fbsde_kernels.cuh.
 //
-// Block: kStepWarps consumer warps + one scalar warp (16 warps: 128 registers a thread).
+// Block: kStepWarps consumer warps + one service warp (16 warps: 128 registers a thread).
 // The CTA owns the contiguous rows [r0, r1) of one query, taken in stages of R rows
 // (R in {1, 3, 5, 15, 30}, R * ld <= kStepElems floats where possible):
+//   load (service warp, one lane)  the rows Delta_{k+1} of stage i + 2 are copied into a
+//                    two-slot shared-memory ring by one bulk copy (cp.async.bulk, completion
+//                    on the slot's mbarrier) as soon as the consumers are done with stage i;
 //   P1 (consumers)   team of T = 480 / R threads per row, VM chunks of 16 bytes each per
-//                    thread: the chunks, loaded two ahead of their use through a register
-//                    FIFO that runs on into the next stage, are stepped, written back to HBM and
-//                    to a shared-memory slot; the four row sums (alpha_x . D, |D|^2,
-//                    sum cos(x0 + D), g . D) go to shared memory per warp (or half-warp);
-//   P2 (scalar warp) lane r handles row r of the stage: FP32 Newton, then FP64 Newton
+//                    thread: the chunks are read from the ring, stepped and written back to
+//                    HBM; the four row sums (alpha_x . D, |D|^2, sum cos(x0 + D), g . D) go
+//                    to shared memory per warp (or half-warp);
+//   P2 (service warp) lane r handles row r of the stage: FP32 Newton, then FP64 Newton
 //                    iterations that decide Y_k (the FP64 dependency chain is the latency
 //                    that matters: 64 cycles per dependent FP64 operation on this part),
 //                    the weight, the three moment coefficients; it runs while the
 //                    consumers step the next stage;
-//   P3 (consumers)   each thread owns fixed column chunks and adds the stage's rows,
-//                    weighted by the three coefficients, into register accumulators.
+//   P3 (consumers)   each thread owns fixed column chunks and adds the stage's updated rows,
+//                    read back from L2 (they were written one stage earlier), weighted by
+//                    the three coefficients, into register accumulators.
 // P3 of stage i-1 follows P1 of stage i, so P2 is off the consumers' critical path.
-// Named barriers: A[b] "row sums of stage i ready" (consumers arrive, scalar warp
-// waits), C[b] "coefficients of stage i ready" (scalar warp arrives, consumers wait),
-// b = i mod 2.  Outputs: the updated rows, Y_k, the weights, per-CTA partial d-vectors
-// (reduced by k_reduce_partials) and per-CTA scalar sums (spart).
+// Hand-offs by mbarriers (b = i mod 2): sums[b] "stage i stepped: row sums written, ring
+// slot free" (every consumer arrives, the service warp waits), coefb[b] "coefficients of
+// stage i ready" (the service warp arrives, each consumer waits on its own), so the
+// consumer warps never wait for one another and a fast warp may run a stage ahead.  Outputs: the updated rows, Y_k, the weights,
+// per-CTA partial d-vectors (reduced by k_reduce_partials) and per-CTA scalar sums (spart).
 #pragma once
-#include "fbsde_kernels.cuh"
+#include "fbsde_matvec.cuh"   // mbarrier and bulk-copy helpers
 
 namespace fbsde {
 namespace dev {
@@ -37,23 +41,37 @@ namespace dev {
 constexpr int kStepWarps = 15;   // + the scalar warp: 16 warps, four per SM sub-partition
 constexpr int kStepConsumers = 32 * kStepWarps;
 constexpr int kStepThreads = kStepConsumers + 32;
-constexpr int kStepBarA = 1, kStepBarC = 3, kStepBarEnd = 5;
-
-__device__ __forceinline__ void bar_arrive_named(int id, int nthreads)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
+constexpr int kStepBarEnd = 5;   // named barrier of the consumers' final reduction
 
 // Philox words of one 16-byte chunk -> the four scaled normals scale * xi (Box-Muller
 // pairs (0,1), (2,3)); bit-identical to normal_chunk for scale = 1.
-__device__ __forceinline__ float4 normals_scaled(uint32_t c, uint32_t j, uint32_t k, uint32_t s,
-                                                 uint32_t k0, uint32_t k1, float scale)
+__device__ __forceinline__ float4 normals_scaled(const Params &p, uint32_t c, uint32_t j,
+                                                 uint32_t k, uint32_t s, float scale)
 {
-    const uint4 w = philox4x32_10(make_uint4(c, j, k, s), k0, k1);
+    const uint4 w = philox4x32_10_rk(make_uint4(c, j, k, s), p.rk0, p.rk1);
     float4 z;
     box_muller_scaled(w.x, w.y, scale, z.x, z.y);
     box_muller_scaled(w.z, w.w, scale, z.z, z.w);
     return z;
+}
+
+// Sum of the four row sums over a warp, scattered: afterwards lanes 8q .. 8q + 7 hold the
+// warp's total of value q (q = 0..3).  Six shuffles instead of twenty: the first two
+// exchanges halve the values each lane carries, the last three sum the one left.
+__device__ __forceinline__ float warp_sum4_scatter(float s0, float s1, float s2, float s3, int lane)
+{
+    const bool hi16 = lane & 16, hi8 = lane & 8;
+    float k0 = hi16 ? s2 : s0, k1 = hi16 ? s3 : s1;
+    const float o0 = hi16 ? s0 : s2, o1 = hi16 ? s1 : s3;
+    k0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+    float k = hi8 ? k1 : k0;
+    const float o = hi8 ? k0 : k1;
+    k += __shfl_xor_sync(0xffffffffu, o, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
 }
 
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
@@ -62,20 +80,6 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
     acc = fmaf(a.y, b.y, acc);
     acc = fmaf(a.z, b.z, acc);
     return fmaf(a.w, b.w, acc);
-}
-
-// Per-element term of the terminal feature sum in FP32 (g_term for Real = float).
-__device__ __forceinline__ float g_term_f(int kind, float x, float th)
-{
-    switch (kind) {
-    case FBSDE_AC_MANUFACTURED:
-    case FBSDE_COS_LINEAR_TEST: return __cosf(x);
-    case FBSDE_LOGISTIC_GRAD: return x;
-    case FBSDE_HJB_LOGQUAD: return th * x * x;
-    case FBSDE_AFFINE_TEST: return th * x;
-    case FBSDE_AC_DOUBLEWELL: return x * x;
-    default: return 0.0f;
-    }
 }
 
 // f(y) and df/dy of the driver for a y-independent feature feat, in the arithmetic of T
@@ -154,32 +158,47 @@ __device__ __forceinline__ double newton_fp32_fp64(const Params &p, double E, fl
 
 // Geometry of the fused step (host-computed, in Params): R rows per stage, T = 480 / R
 // threads per row in P1 with VM chunks each (VM = ceil(nch / T), the template argument);
-// P3 row groups of tpr threads (RG of them), vm3 <= VM chunks per thread; nslot
-// shared-memory row slots.
-template <int VM, bool COSF, bool TERM>
+// P3 row groups of tpr threads (RG of them), vm3 <= VM chunks per thread.  ONE: the
+// one-row stage (R = 1, T = tpr = 480, rows wider than
+// 3413 floats) with its strides known at compile time; its chunks v < VM - 1 always lie
+// inside the row.
+template <int VM, bool COSF, bool TERM, bool ONE>
 __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
 {
     // chunks of the column pass held in registers; its sixth chunk (R = 1 with rows wider
     // than 9600 floats) accumulates in shared memory
     constexpr int VMR = VM < 5 ? VM : 5;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int g = blockIdx.x, s = blockIdx.y;
     const WS<float> ws(p);
     SolveState &st = p.st[s];
     constexpr bool terminal = TERM;
     const int ld = p.ld, nch = ld >> 2, d = p.d;
-    const int R = p.st_R, T = p.st_T, nslot = p.st_nslot;
+    const int R = ONE ? 1 : p.st_R, T = ONE ? kStepConsumers : p.st_T;
     float *vx = reinterpret_cast<float *>(smem_raw);   // alpha_x (terminal: unused)
     float *vg = vx + ld;                                // g (terminal: theta)
     float *vx0 = vg + ld;                               // x0
-    float *slots = vx0 + ld;                            // [nslot][R][ld]
+    float *ring = vx0 + ld;                             // [2][R][ld] rows Delta_{k+1}
     const size_t slot_floats = (size_t)R * ld;
-    float4 *wsum = reinterpret_cast<float4 *>(slots + p.st_region);   // [2][32]
+    float4 *wsum = reinterpret_cast<float4 *>(ring + p.st_region);    // [2][32]
     float4 *coef = wsum + 64;                                            // [2][32]
-    float4 *tail = coef + 64;   // [3][nch - 5 kStepConsumers] column-pass chunks v = 5
+    // mbarriers: full[2] ring slot loaded (bulk-copy bytes), sums[2] row sums of a stage
+    // written by every consumer thread, coefb[2] coefficients of a stage written by the
+    // service warp; slot / buffer b = stage mod 2
+    uint64_t *full = reinterpret_cast<uint64_t *>(coef + 64);
+    uint64_t *sums = full + 2, *coefb = full + 4;
+    float4 *tail = reinterpret_cast<float4 *>(full + 6);  // [3][nch - 5 kStepConsumers]
     const bool has_tail = VM > 5 && p.st_vm3 > 5;   // only with R = 1 and nch > 2400
     const int ntail = has_tail ? nch - 5 * kStepConsumers : 0;
     for (int i = threadIdx.x; i < 3 * ntail; i += blockDim.x) tail[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&sums[b], kStepConsumers);
+            mbar_init(&coefb[b], 32);
+        }
+        fence_mbar_init();
+    }
 
     const uint32_t sidx = p.solve0 + (uint32_t)s;
     for (int i = threadIdx.x; i < ld; i += blockDim.x) {
@@ -194,8 +213,23 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
     const int nst = (int)((r1 - r0 + R - 1) / R);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    bool timed_out = false;
+    const uint32_t row_bytes = (uint32_t)ld * sizeof(float);
+    // bulk copy of the rows of stage i into ring slot i mod 2 (one lane of the service warp)
+    auto load_stage = [&](int i) {
+        const long long base = r0 + (long long)i * R;
+        const uint32_t rows = (uint32_t)min((long long)R, r1 - base);
+        uint64_t *bar = &full[i & 1];
+        mbar_arrive_expect_tx(bar, rows * row_bytes);
+        bulk_g2s(ring + (size_t)(i & 1) * slot_floats, ws.row(s, base), rows * row_bytes, bar);
+    };
+
     if (warp == kStepWarps) {
-        // ---------------- P2: the scalar warp ----------------
+        // ---------------- the service warp: ring loads and P2 ----------------
+        if (!terminal && lane == 0) {
+            if (nst > 0) load_stage(0);
+            if (nst > 1) load_stage(1);
+        }
         const int PW = T >= 32 ? T >> 5 : 1;          // partial sums per row
         const double t_k = p.level * p.dt;
         const double rho_ref = p.sigma * p.sigma * p.d * t_k;
@@ -206,13 +240,16 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
         const float lc_f = (float)lc_d;
         const double yref = terminal ? st.gx0 : st.alpha;
         const double feat_level = terminal ? 0.0 : f_feature(p, t_k, 0.0, st.sumz, st.zz);
+        const bool cos_g = p.kind == FBSDE_AC_MANUFACTURED || p.kind == FBSDE_COS_LINEAR_TEST;
         double accW = 0.0, accC = 0.0, accR = 0.0;
         int it_max = 0, failed = 0;
         for (int i = 0; i < nst; ++i) {
             const int b = i & 1;
             const long long base = r0 + (long long)i * R;
             const int nrows = (int)min((long long)R, r1 - base);
-            bar_named(kStepBarA + b, kStepThreads);
+            mbar_wait_or_flag(&sums[b], (uint32_t)((i >> 1) & 1), timed_out);
+            // the consumers are done with slot i mod 2: refill it with stage i + 2
+            if (!terminal && lane == 0 && i + 2 < nst) load_stage(i + 2);
             if (lane < nrows) {
                 const long long j = base + lane;
                 float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
@@ -227,7 +264,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
                 float gd = 0.0f;
                 if (terminal) {
                     rho = (double)a0;
-                    Yj = g_value(p, (double)a1);
+                    Yj = g_value(p, (double)a1 - (cos_g ? (double)(ld - d) : 0.0));
                 } else {
                     rho = (double)a1;
                     gd = a3;
@@ -260,8 +297,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
                 accC = fma(wd, dY, accC);
                 accR = fma(wd, rho, accR);
             }
-            __syncwarp();
-            bar_arrive_named(kStepBarC + b, kStepThreads);
+            mbar_arrive(&coefb[b]);
         }
         // per-CTA scalar sums in lane order (fixed), Newton statistics
 #pragma unroll
@@ -272,6 +308,11 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
             it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
         }
         const bool any_failed = __any_sync(0xffffffffu, failed);
+        if (!terminal && lane == 0) {   // every copy issued has landed before the CTA exits
+            for (int i = max(0, nst - 2); i < nst; ++i)
+                mbar_wait_or_flag(&full[i & 1], (uint32_t)((i >> 1) & 1), timed_out);
+        }
+        if (timed_out) atomicCAS(&st.status, 0, (int)FBSDE_ERR_TIMEOUT);
         if (lane == 0) {
             double *o = ws.spart(s, g);
             o[0] = accW;
@@ -290,88 +331,87 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
 
     // ---------------- consumers: P1 and P3 ----------------
     const int ct = threadIdx.x;                 // 0 .. kStepConsumers - 1
-    const int team = ct / T, tl = ct - team * T;
-    const int red_from = T >= 32 ? 16 : (T >> 1);
-    const int pidx = T >= 32 ? warp : (ct >> 4);   // partial-sum slot of this (half-)warp
-    const bool writer = T >= 32 ? lane == 0 : (lane & 15) == 0;
-    const int tpr = p.st_tpr, RG = p.st_RG, vm3 = p.st_vm3;
-    const int rg = ct / tpr, tc = ct - rg * tpr;
+    const int team = ONE ? 0 : ct / T, tl0 = ONE ? ct : ct - team * T;
+    const int tpr = ONE ? kStepConsumers : p.st_tpr, RG = ONE ? 1 : p.st_RG;
+    const int vm3 = ONE ? VM : p.st_vm3;
+    const int rg = ONE ? 0 : ct / tpr, tc = ONE ? ct : ct - rg * tpr;
     const float wa = (float)p.wa, wb = (float)p.wb;
     const uint32_t kk = (uint32_t)p.level;
+    // chunk v = tl + T v of a row exists (ONE: every v < VM - 1 does)
+    auto in_row = [&](int v, int c) { return (ONE && v < VM - 1) || c < nch; };
     float4 acc[3][VMR];
 #pragma unroll
     for (int v = 0; v < VMR; ++v)
         acc[0][v] = acc[1][v] = acc[2][v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // The rows this thread reads, Delta_{k+1}: chunk v of stage i sits at FIFO position
-    // i VM + v; cur / nxt hold positions q and q + 1 while position q is stepped, and the
-    // load of position q + 2 is issued then.  row_of(i) is the team's row of stage i, or
-    // null past the CTA's rows.
-    // row_of(i): the team's row of stage i, or null past the CTA's rows; the row of stage
-    // i + a is a R ld floats further on.
-    auto row_of = [&](int i) -> const float4 * {
-        const long long j = r0 + (long long)i * R + team;
-        return (!terminal && i < nst && j < r1) ? reinterpret_cast<const float4 *>(ws.row(s, j))
-                                                : nullptr;
+    // fma of one chunk of a row into the three accumulators of chunk v
+    auto acc3 = [&](float4 (&a)[3], const float4 cf, const float4 x) {
+        a[0].x = fmaf(cf.x, x.x, a[0].x);
+        a[0].y = fmaf(cf.x, x.y, a[0].y);
+        a[0].z = fmaf(cf.x, x.z, a[0].z);
+        a[0].w = fmaf(cf.x, x.w, a[0].w);
+        a[1].x = fmaf(cf.y, x.x, a[1].x);
+        a[1].y = fmaf(cf.y, x.y, a[1].y);
+        a[1].z = fmaf(cf.y, x.z, a[1].z);
+        a[1].w = fmaf(cf.y, x.w, a[1].w);
+        a[2].x = fmaf(cf.z, x.x, a[2].x);
+        a[2].y = fmaf(cf.z, x.y, a[2].y);
+        a[2].z = fmaf(cf.z, x.z, a[2].z);
+        a[2].w = fmaf(cf.z, x.w, a[2].w);
     };
-    const int stage_chunks = R * (ld >> 2);
-    float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
-    {
-        const float4 *q0 = row_of(0), *q1 = row_of(VM > 1 ? 0 : 1);
-        const int c0 = tl, c1 = tl + T * (VM > 1 ? 1 : 0);
-        if (q0 && c0 < nch) cur = __ldcs(q0 + c0);
-        if (q1 && c1 < nch) nxt = __ldcs(q1 + c1);
-    }
-
     auto p3 = [&](int i) {
         const int b = i & 1;
         const long long base = r0 + (long long)i * R;
-        const int nrows = (int)min((long long)R, r1 - base);
-        bar_named(kStepBarC + b, kStepThreads);
+        const int nrows = ONE ? 1 : (int)min((long long)R, r1 - base);
+        if (ONE) {
+            // the row stepped in P1 of stage i, read back through L2.  With one row per
+            // stage the row pass and the column pass own the same chunks, so these are this
+            // thread's own stores and the loads can be issued before the wait for the
+            // stage's coefficients.
+            const float4 *row = reinterpret_cast<const float4 *>(ws.row(s, base));
+            float4 x[VM];
+#pragma unroll
+            for (int v = 0; v < VM; ++v) {
+                const int c = tc + tpr * v;
+                if (in_row(v, c)) x[v] = __ldcg(row + c);
+            }
+            mbar_wait_or_flag(&coefb[b], (uint32_t)((i >> 1) & 1), timed_out);
+            const float4 cf = coef[b * 32];
+#pragma unroll
+            for (int v = 0; v < VMR; ++v) {
+                float4 a[3] = {acc[0][v], acc[1][v], acc[2][v]};
+                if (in_row(v, tc + tpr * v)) acc3(a, cf, x[v]);
+                acc[0][v] = a[0];
+                acc[1][v] = a[1];
+                acc[2][v] = a[2];
+            }
+            if (VM > 5 && has_tail) {
+                const int c = tc + tpr * 5;
+                if (c < nch) {
+                    float4 *t0 = tail + (c - 5 * kStepConsumers);
+                    float4 a[3] = {t0[0], t0[ntail], t0[2 * ntail]};
+                    acc3(a, cf, x[VM - 1]);
+                    t0[0] = a[0];
+                    t0[ntail] = a[1];
+                    t0[2 * ntail] = a[2];
+                }
+            }
+            return;
+        }
+        mbar_wait_or_flag(&coefb[b], (uint32_t)((i >> 1) & 1), timed_out);
         if (rg < RG) {
-            const float *sl = slots + (size_t)(i % nslot) * slot_floats;
             for (int r = rg; r < nrows; r += RG) {
                 const float4 cf = coef[b * 32 + r];
-                const float4 *row = reinterpret_cast<const float4 *>(sl + (size_t)r * ld);
-                if (VM > 5 && has_tail) {
-                    const int c = tc + tpr * 5;
-                    if (c < nch) {
-                        const float4 x = row[c];
-                        float4 *t0 = tail + (c - 5 * kStepConsumers);
-                        float4 a0 = t0[0], a1 = t0[ntail], a2 = t0[2 * ntail];
-                        a0.x = fmaf(cf.x, x.x, a0.x);
-                        a0.y = fmaf(cf.x, x.y, a0.y);
-                        a0.z = fmaf(cf.x, x.z, a0.z);
-                        a0.w = fmaf(cf.x, x.w, a0.w);
-                        a1.x = fmaf(cf.y, x.x, a1.x);
-                        a1.y = fmaf(cf.y, x.y, a1.y);
-                        a1.z = fmaf(cf.y, x.z, a1.z);
-                        a1.w = fmaf(cf.y, x.w, a1.w);
-                        a2.x = fmaf(cf.z, x.x, a2.x);
-                        a2.y = fmaf(cf.z, x.y, a2.y);
-                        a2.z = fmaf(cf.z, x.z, a2.z);
-                        a2.w = fmaf(cf.z, x.w, a2.w);
-                        t0[0] = a0;
-                        t0[ntail] = a1;
-                        t0[2 * ntail] = a2;
-                    }
-                }
+                // the row stepped in P1 of stage i, read back through L2
+                const float4 *row = reinterpret_cast<const float4 *>(ws.row(s, base + r));
 #pragma unroll
                 for (int v = 0; v < VMR; ++v) {
                     const int c = tc + tpr * v;
                     if (v < vm3 && c < nch) {
-                        const float4 x = row[c];
-                        acc[0][v].x = fmaf(cf.x, x.x, acc[0][v].x);
-                        acc[0][v].y = fmaf(cf.x, x.y, acc[0][v].y);
-                        acc[0][v].z = fmaf(cf.x, x.z, acc[0][v].z);
-                        acc[0][v].w = fmaf(cf.x, x.w, acc[0][v].w);
-                        acc[1][v].x = fmaf(cf.y, x.x, acc[1][v].x);
-                        acc[1][v].y = fmaf(cf.y, x.y, acc[1][v].y);
-                        acc[1][v].z = fmaf(cf.y, x.z, acc[1][v].z);
-                        acc[1][v].w = fmaf(cf.y, x.w, acc[1][v].w);
-                        acc[2][v].x = fmaf(cf.z, x.x, acc[2][v].x);
-                        acc[2][v].y = fmaf(cf.z, x.y, acc[2][v].y);
-                        acc[2][v].z = fmaf(cf.z, x.z, acc[2][v].z);
-                        acc[2][v].w = fmaf(cf.z, x.w, acc[2][v].w);
+                        float4 a[3] = {acc[0][v], acc[1][v], acc[2][v]};
+                        acc3(a, cf, __ldcg(row + c));
+                        acc[0][v] = a[0];
+                        acc[1][v] = a[1];
+                        acc[2][v] = a[2];
                     }
                 }
             }
@@ -381,92 +421,103 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
     for (int i = 0; i < nst; ++i) {
         const int b = i & 1;
         const long long base = r0 + (long long)i * R;
-        const int nrows = (int)min((long long)R, r1 - base);
+        const int nrows = ONE ? 1 : (int)min((long long)R, r1 - base);
+        const bool active = ONE || team < nrows;
+        const int tl = tl0;
         const long long j = base + team;
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        float4 *dst = reinterpret_cast<float4 *>(ws.row(s, team < nrows ? j : base));
-        float4 *sl = reinterpret_cast<float4 *>(slots + (size_t)(i % nslot) * slot_floats +
-                                                (size_t)team * ld);
+        float4 *dst = reinterpret_cast<float4 *>(ws.row(s, active ? j : base));
         if (terminal) {
-            if (team < nrows) {
+            if (active) {
                 const int kind = p.kind;
 #pragma unroll
                 for (int v = 0; v < VM; ++v) {
                     const int c = tl + T * v;
-                    if (c < nch) {
-                        float4 z = normals_scaled((uint32_t)c, (uint32_t)j, kk, sidx, p.key0,
-                                                  p.key1, wb);
-                        const float4 x0c = reinterpret_cast<const float4 *>(vx0)[c];
-                        const float4 thc = reinterpret_cast<const float4 *>(vg)[c];
-                        const int i0 = 4 * c;
-                        if (i0 + 1 >= d) z.y = 0.0f;
-                        if (i0 + 2 >= d) z.z = 0.0f;
-                        if (i0 + 3 >= d) z.w = 0.0f;
+                    if (in_row(v, c)) {
+                        float4 z = normals_scaled(p, (uint32_t)c, (uint32_t)j, kk, sidx, wb);
+                        if ((!ONE || v == VM - 1) && 4 * c + 4 > d) {   // padding stays 0
+                            const int i0 = 4 * c;
+                            if (i0 + 1 >= d) z.y = 0.0f;
+                            if (i0 + 2 >= d) z.z = 0.0f;
+                            if (i0 + 3 >= d) z.w = 0.0f;
+                        }
                         s0 = dot4(z, z, s0);
-                        s1 += g_term_f(kind, x0c.x + z.x, thc.x);
-                        if (i0 + 1 < d) s1 += g_term_f(kind, x0c.y + z.y, thc.y);
-                        if (i0 + 2 < d) s1 += g_term_f(kind, x0c.z + z.z, thc.z);
-                        if (i0 + 3 < d) s1 += g_term_f(kind, x0c.w + z.w, thc.w);
-                        sl[c] = z;
-                        __stcs(dst + c, z);
+                        // terminal feature of g at x0 + Delta_N (padding: x0 = theta = 0, so
+                        // only the cosine kinds see it, as cos 0 = 1, removed in P2)
+                        const float4 xc = reinterpret_cast<const float4 *>(vx0)[c];
+                        const float4 x = make_float4(xc.x + z.x, xc.y + z.y, xc.z + z.z, xc.w + z.w);
+                        if (kind == FBSDE_AC_MANUFACTURED || kind == FBSDE_COS_LINEAR_TEST) {
+                            s1 += (cos_ftz(x.x) + cos_ftz(x.y)) + (cos_ftz(x.z) + cos_ftz(x.w));
+                        } else if (kind == FBSDE_LOGISTIC_GRAD) {
+                            s1 += (x.x + x.y) + (x.z + x.w);
+                        } else if (kind == FBSDE_AC_DOUBLEWELL) {
+                            s1 = dot4(x, x, s1);
+                        } else if (kind == FBSDE_HJB_LOGQUAD || kind == FBSDE_AFFINE_TEST) {
+                            const float4 th = reinterpret_cast<const float4 *>(vg)[c];
+                            const float4 tx = make_float4(th.x * x.x, th.y * x.y, th.z * x.z,
+                                                          th.w * x.w);
+                            s1 = kind == FBSDE_HJB_LOGQUAD ? dot4(tx, x, s1)
+                                                           : s1 + ((tx.x + tx.y) + (tx.z + tx.w));
+                        }
+                        dst[c] = z;
                     }
                 }
             }
         } else {
-            const float4 *ahead0 = row_of(i);
-            const bool has1 = i + 1 < nst && j + R < r1, has2 = i + 2 < nst && j + 2 * R < r1;
+            mbar_wait_or_flag(&full[b], (uint32_t)((i >> 1) & 1), timed_out);
+            const float4 *sl = reinterpret_cast<const float4 *>(ring + (size_t)b * slot_floats +
+                                                                (size_t)team * ld);
+            if (active) {
 #pragma unroll
-            for (int v = 0; v < VM; ++v) {
-                const int c = tl + T * v;
-                const float4 dold = cur;
-                cur = nxt;
-                {   // load FIFO position i VM + v + 2
-                    const int vq = (v + 2) % VM, iq = (v + 2) / VM;
-                    const bool has = iq == 0 ? (ahead0 != nullptr) : (iq == 1 ? has1 : has2);
-                    const int cq = tl + T * vq;
-                    if (has && cq < nch) nxt = __ldcs(ahead0 + (size_t)iq * stage_chunks + cq);
-                }
-                if (team < nrows && c < nch) {
-                    float4 z = normals_scaled((uint32_t)c, (uint32_t)j, kk, sidx, p.key0,
-                                              p.key1, wb);
-                    if (4 * c + 4 > d) {   // the row's last chunk: padding stays zero
-                        const int i0 = 4 * c;
-                        if (i0 + 1 >= d) z.y = 0.0f;
-                        if (i0 + 2 >= d) z.z = 0.0f;
-                        if (i0 + 3 >= d) z.w = 0.0f;
+                for (int v = 0; v < VM; ++v) {
+                    const int c = tl + T * v;
+                    if (in_row(v, c)) {
+                        const float4 dold = sl[c];
+                        float4 z = normals_scaled(p, (uint32_t)c, (uint32_t)j, kk, sidx, wb);
+                        if ((!ONE || v == VM - 1) && 4 * c + 4 > d) {   // padding stays 0
+                            const int i0 = 4 * c;
+                            if (i0 + 1 >= d) z.y = 0.0f;
+                            if (i0 + 2 >= d) z.z = 0.0f;
+                            if (i0 + 3 >= d) z.w = 0.0f;
+                        }
+                        float4 dn;
+                        dn.x = fmaf(wa, dold.x, z.x);
+                        dn.y = fmaf(wa, dold.y, z.y);
+                        dn.z = fmaf(wa, dold.z, z.z);
+                        dn.w = fmaf(wa, dold.w, z.w);
+                        const float4 ax = reinterpret_cast<const float4 *>(vx)[c];
+                        const float4 gg = reinterpret_cast<const float4 *>(vg)[c];
+                        s0 = dot4(ax, dn, s0);
+                        s1 = dot4(dn, dn, s1);
+                        s3 = dot4(gg, dn, s3);
+                        if (COSF) {
+                            const float4 xc = reinterpret_cast<const float4 *>(vx0)[c];
+                            s2 += (cos_ftz(xc.x + dn.x) + cos_ftz(xc.y + dn.y)) +
+                                  (cos_ftz(xc.z + dn.z) + cos_ftz(xc.w + dn.w));
+                        }
+                        dst[c] = dn;
                     }
-                    float4 dn;
-                    dn.x = fmaf(wa, dold.x, z.x);
-                    dn.y = fmaf(wa, dold.y, z.y);
-                    dn.z = fmaf(wa, dold.z, z.z);
-                    dn.w = fmaf(wa, dold.w, z.w);
-                    const float4 ax = reinterpret_cast<const float4 *>(vx)[c];
-                    const float4 gg = reinterpret_cast<const float4 *>(vg)[c];
-                    s0 = dot4(ax, dn, s0);
-                    s1 = dot4(dn, dn, s1);
-                    s3 = dot4(gg, dn, s3);
-                    if (COSF) {
-                        const float4 xc = reinterpret_cast<const float4 *>(vx0)[c];
-                        s2 += (__cosf(xc.x + dn.x) + __cosf(xc.y + dn.y)) +
-                              (__cosf(xc.z + dn.z) + __cosf(xc.w + dn.w));
-                    }
-                    sl[c] = dn;
-                    __stcs(dst + c, dn);
                 }
             }
         }
-        for (int o = red_from; o; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        if (T >= 32) {   // one partial per warp; lane 8q writes component q
+            const float k4 = warp_sum4_scatter(s0, s1, s2, s3, lane);
+            if ((lane & 7) == 0) reinterpret_cast<float *>(wsum + b * 32 + warp)[lane >> 3] = k4;
+        } else {         // half-warp teams: one partial per half-warp
+#pragma unroll
+            for (int o = 8; o; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            }
+            if ((lane & 15) == 0) wsum[b * 32 + (ct >> 4)] = make_float4(s0, s1, s2, s3);
         }
-        if (writer) wsum[b * 32 + pidx] = make_float4(s0, s1, s2, s3);
-        __syncwarp();
-        bar_arrive_named(kStepBarA + b, kStepThreads);
+        mbar_arrive(&sums[b]);
         if (i >= 1) p3(i - 1);
     }
     if (nst >= 1) p3(nst - 1);
+    if (timed_out) atomicCAS(&st.status, 0, (int)FBSDE_ERR_TIMEOUT);
 
     // per-CTA partial d-vectors: row groups summed in group order (threads past the RG
     // row groups of tpr threads own no chunk)
@@ -478,7 +529,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
 #pragma unroll
             for (int v = 0; v < VMR; ++v) {
                 const int c = tc + tpr * v;
-                if (v < vm3 && c < nch) dst[c] = acc[a][v];
+                if (v < vm3 && in_row(v, c)) dst[c] = acc[a][v];
             }
             if (VM > 5 && has_tail) {
                 const int c = tc + tpr * 5;
@@ -487,8 +538,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
         }
         return;
     }
-    bar_named(kStepBarEnd, kStepConsumers);   // every consumer is past its last slot read
-    float4 *red = reinterpret_cast<float4 *>(slots);  // [RG][3][nch]
+    bar_named(kStepBarEnd, kStepConsumers);   // every consumer is past its last ring read
+    float4 *red = reinterpret_cast<float4 *>(ring);   // [RG][3][nch]
     if (rg < RG) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)

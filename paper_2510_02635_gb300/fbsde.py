@@ -556,6 +556,9 @@ def _main(argv=None) -> None:
                     help="run the launch profiler on the product kernel (the first "
                          "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
                          "one by one, outside CUDA graphs, e.g. for a kernel profiler)")
+    ap.add_argument("--time-family", default=None,
+                    help="time the launches of one kernel family (e.g. step) with the "
+                         "library's launch profiler")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
     x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)) if a.x0 == "uniform"
@@ -563,9 +566,9 @@ def _main(argv=None) -> None:
     theta = rng.uniform(0.5, 1.5, size=a.d) if a.kind in ("hjb_logquad", "affine_test") else None
     solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
                     theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
-    if a.time_products:
+    if a.time_products or a.time_family:
         fbsde_profile_start(1 << 20)
-        fbsde_profile_select(["matvec"])
+        fbsde_profile_select([a.time_family or "matvec"])
     for r in range(a.repeat):
         t0 = time.perf_counter()
         out = (solve_anchored(solver.problem, x0, a.seed) if a.anchored
@@ -574,10 +577,11 @@ def _main(argv=None) -> None:
         dt = time.perf_counter() - t0
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
               f"u0[0]={float(out['u0'][0]):.12f}")
-    if a.time_products:
-        mv = fbsde_profile_stop()["matvec"]
-        print(f"product launches {mv['launches']}, timed {mv['timed']}, "
-              f"{mv['total_ms']:.2f} ms")
+    if a.time_products or a.time_family:
+        fam = a.time_family or "matvec"
+        mv = fbsde_profile_stop()[fam]
+        print(f"{fam} launches {mv['launches']}, timed {mv['timed']}, "
+              f"{mv['total_ms']:.3f} ms")
 
 
 if __name__ == "__main__":
