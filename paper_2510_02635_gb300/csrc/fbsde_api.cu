@@ -120,7 +120,24 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
             L.st_smem > 227 * 1024)
             return FBSDE_ERR_ARG;
     }
-    L.GS = std::max(L.GP, L.fused ? L.G : 0);
+    // CTAs per query of the fused step (one CTA per SM): whole waves of 152 CTAs where
+    // possible, at least four stages per CTA; 4..1 waves first, then 5..8
+    L.Gs = L.G;
+    if (L.fused) {
+        const long long gmax_s = std::max<long long>(1, P->M / (4LL * L.st_R));
+        double best = -1.0;
+        for (int W : {4, 3, 2, 1, 5, 6, 7, 8}) {
+            const long long g = std::min<long long>(gmax_s, (152LL * W + Q - 1) / Q);
+            const double waves = (double)(g * Q) / 152.0;
+            const double eff = waves / std::ceil(waves);
+            if (eff > best + 1e-9) {
+                best = eff;
+                L.Gs = (int)g;
+            }
+            if (eff >= 0.99) break;
+        }
+    }
+    L.GS = std::max(L.GP, L.fused ? L.Gs : 0);
     // partial reduction: tiles of kRedTile elements, red_groups warps per tile, each adding
     // about four of the G partials
     L.nblk = (L.ld + kRedTile - 1) / kRedTile;
@@ -140,7 +157,7 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_w = take(Qs * Ms * L.real_sz);
     L.off_coef = take(Qs * Ms * 3 * L.real_sz);
     L.off_segp = take(Qs * Ms * (size_t)L.nseg * kSegSums * L.real_sz);
-    L.off_part = take(Qs * L.G * kPartVecs * lds * L.real_sz);
+    L.off_part = take(Qs * std::max(L.G, L.Gs) * kPartVecs * lds * L.real_sz);
     L.off_spart = take(Qs * L.GS * kPartScal * sizeof(double));
     L.off_vec64 = take(Qs * kVec64 * lds * sizeof(double));
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
@@ -170,7 +187,7 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
     p.nseg = L.nseg;
     p.GP = L.GP;
     p.GS = L.GS;
-    p.nsp = L.fused ? L.G : L.GP;
+    p.nsp = L.fused ? L.Gs : L.GP;
     p.st_R = L.st_R;
     p.st_T = L.st_T;
     p.st_vm1 = L.st_vm1;
@@ -459,16 +476,21 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
     cudaError_t e;
     const cudaStream_t s = r.s;
     FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, s));
+    // the fused step tiles the rows over L.Gs CTAs per query: its partial vectors are
+    // reduced with that count (the products keep L.G)
+    Params ps = p;
+    ps.G = L.Gs;
+    ps.level = p.N;
     p.level = p.N;
     if (L.fused) {   // forward sweep end point, g and the first regression's moments in one pass
-        FBSDE_TRY(FBSDE_K_STEP, LR::step(p, L, s));
+        FBSDE_TRY(FBSDE_K_STEP, LR::step(ps, L, s));
     } else {
         FBSDE_TRY(FBSDE_K_FORWARD, LR::forward(p, L, s));
         FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
     }
     if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
     if (!L.fused) FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
-    FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+    FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(ps, L, 3, 3, 0, s));
     p.newton_level = -1;
     FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 0, s));
     for (int k = p.N - 1; k >= 0; --k) {
@@ -477,13 +499,16 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
         FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
         if (k >= 1) {
             if (L.fused) {   // the whole level step in one pass over the rows
-                FBSDE_TRY(FBSDE_K_STEP, LR::step(p, L, s));
+                ps = p;
+                ps.G = L.Gs;
+                FBSDE_TRY(FBSDE_K_STEP, LR::step(ps, L, s));
+                FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(ps, L, 3, 3, 0, s));
             } else {
                 FBSDE_TRY(FBSDE_K_UPDATE, LR::update(p, L, s));
                 FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
                 FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+                FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
             }
-            FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
             p.newton_level = k;
             FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
         }

@@ -61,7 +61,7 @@ struct Layout {
     size_t mv_smem;
     // fused per-level step (FP32 rows of at most kStepMaxLd floats): rows per stage, threads
     // per row, chunks per thread in the row pass, column-pass row groups, shared memory
-    int fused, st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_vm, st_nslot, GS;
+    int fused, st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_vm, st_nslot, GS, Gs;
     size_t st_region, st_smem;
     int64_t M;
     size_t real_sz;

@@ -1076,13 +1076,18 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     const int s = blockIdx.x;
     const WS<Real> ws(p);
     SolveState &st = p.st[s];
-    double W = 0.0, Cp = 0.0, Rr = 0.0;
-    for (int b = 0; b < p.nsp; ++b) {
+    // per-block scalar sums (W, sum w (Y - yref), sum w |D|^2): strided over the threads,
+    // then the block tree (fixed order; a serial FP64 chain over hundreds of blocks would
+    // cost 64 cycles per dependent add)
+    double ws3[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < p.nsp; b += blockDim.x) {
         const double *sp = ws.spart(s, b);
-        W += sp[0];
-        Cp += sp[1];
-        Rr += sp[2];
+        ws3[0] += sp[0];
+        ws3[1] += sp[1];
+        ws3[2] += sp[2];
     }
+    block_sum(ws3, sm);
+    const double W = ws3[0], Cp = ws3[1], Rr = ws3[2];
     const double invW = 1.0 / W, cp = Cp * invW;
     double *x = ws.v64(s, 0), *r = ws.v64(s, 1), *pp = ws.v64(s, 2), *S = ws.v64(s, 3),
            *B = ws.v64(s, 4), *Gx = ws.v64(s, 5);

@@ -88,7 +88,7 @@ static cudaError_t launch_step(const Params &q, const Layout &L, cudaStream_t s)
 {
     cudaError_t e = set_smem(dev::k_step<VM, COSF, TERM, ONE>, L.st_smem);
     if (e != cudaSuccess) return e;
-    dev::k_step<VM, COSF, TERM, ONE><<<dim3(L.G, L.Q), dev::kStepThreads, L.st_smem, s>>>(q);
+    dev::k_step<VM, COSF, TERM, ONE><<<dim3(q.G, L.Q), dev::kStepThreads, L.st_smem, s>>>(q);
     return cudaGetLastError();
 }
 

@@ -557,8 +557,8 @@ def _main(argv=None) -> None:
                          "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
                          "one by one, outside CUDA graphs, e.g. for a kernel profiler)")
     ap.add_argument("--time-family", default=None,
-                    help="time the launches of one kernel family (e.g. step) with the "
-                         "library's launch profiler")
+                    help="time the launches of one kernel family (e.g. step), or of "
+                         "every family (all), with the library's launch profiler")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
     x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)) if a.x0 == "uniform"
@@ -568,7 +568,8 @@ def _main(argv=None) -> None:
                     theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
     if a.time_products or a.time_family:
         fbsde_profile_start(1 << 20)
-        fbsde_profile_select([a.time_family or "matvec"])
+        if a.time_family != "all":
+            fbsde_profile_select([a.time_family or "matvec"])
     for r in range(a.repeat):
         t0 = time.perf_counter()
         out = (solve_anchored(solver.problem, x0, a.seed) if a.anchored
@@ -578,10 +579,12 @@ def _main(argv=None) -> None:
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
               f"u0[0]={float(out['u0'][0]):.12f}")
     if a.time_products or a.time_family:
-        fam = a.time_family or "matvec"
-        mv = fbsde_profile_stop()[fam]
-        print(f"{fam} launches {mv['launches']}, timed {mv['timed']}, "
-              f"{mv['total_ms']:.3f} ms")
+        prof = fbsde_profile_stop()
+        for fam in (prof if a.time_family == "all" else [a.time_family or "matvec"]):
+            mv = prof[fam]
+            if mv["launches"]:
+                print(f"{fam} launches {mv['launches']}, timed {mv['timed']}, "
+                      f"{mv['total_ms']:.3f} ms")
 
 
 if __name__ == "__main__":
