@@ -54,6 +54,65 @@ def _matvec_traffic(w: W.Workload) -> float | None:
             + float(kv["write_bytes_per_cta"][0]) * ctas)
 
 
+def _step_traffic(w: W.Workload) -> float | None:
+    """DRAM bytes of the fused step's launches in one solve (N - 1 level steps; the
+    terminal launch writes only), scaled from the ncu capture in profiles/step_traffic.txt;
+    None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_traffic.txt")
+    try:
+        lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    kv = {ln[0]: ln[1:] for ln in lines}
+    src = os.path.join(ROOT, kv["kernel_source"][2])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != kv["kernel_source"][1]:
+        return None
+    pd = w.Q * w.M * w.d
+    rd, wr = float(kv["read_bytes_per_particle_dim"][0]), float(kv["write_bytes_per_particle_dim"][0])
+    return (rd + wr) * pd * (w.N - 1) + wr * pd
+
+
+def _accuracy(w: W.Workload, u: "np.ndarray", grad: "np.ndarray") -> dict:
+    """Error of every query's u(0, x0) and grad u(0, x0) against the workload's closed
+    form, and of query 0 against the FP64 oracle's solve of the same stream (stored by
+    tests/golden/make_closed_form_bounds.py, valid while the oracle source is unchanged),
+    with the scheme's own error bound from that oracle sweep."""
+    import hashlib
+
+    import numpy as np
+    x0 = W.inputs(w)["x0"]
+    eu, eg = [], []
+    for q in range(u.shape[0]):
+        us, gs = W.exact_solution(w, x0[q % x0.shape[0]])
+        eu.append(abs(float(u[q]) - us) / abs(us))
+        eg.append(float(np.linalg.norm(grad[q] - gs) / np.linalg.norm(gs)))
+    out = {"closed_form": {"rel_err_u": eu, "rel_err_grad": eg, "max_rel_err_u": max(eu),
+                           "max_rel_err_grad": max(eg)}}
+    path = os.path.join(ROOT, "tests", "golden", "closed_form_bounds.json")
+    try:
+        ref = json.load(open(path))
+    except OSError:
+        out["vs_oracle"] = {"unavailable": "no stored oracle solve"}
+        return out
+    src = hashlib.sha256(open(os.path.join(ROOT, "oracle", "fbsde_oracle.c"), "rb").read()).hexdigest()
+    entry = ref["workloads"].get(w.name)
+    if entry is None or src != ref["oracle_source_sha256"]:
+        out["vs_oracle"] = {"unavailable": "stored oracle solve is stale or missing"}
+        return out
+    o = entry["oracle_query0"]
+    og = np.asarray(o["grad"])
+    out["vs_oracle"] = {"query": 0, "rel_err_u": abs(float(u[0]) - o["u0"]) / abs(o["u0"]),
+                        "rel_err_grad": float(np.linalg.norm(grad[0] - og) /
+                                              max(np.linalg.norm(og), abs(o["u0"]))),
+                        "tolerance": 1e-4}
+    out["scheme_bound"] = {"rel_err_u": entry["u"]["bound"], "rel_err_grad": entry["grad"]["bound"],
+                           "streams": entry["streams"], "rule": ref["bound_rule"],
+                           "all_queries_within": bool(max(eu) <= entry["u"]["bound"] and
+                                                      max(eg) <= entry["grad"]["bound"])}
+    return out
+
+
 def _peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -147,6 +206,57 @@ def oracle_sample(w: W.Workload, levels: int = 2) -> dict:
             "sample": (f"1 of {w.Q} queries (d={w.d}, M={w.M}), full forward sweep of "
                        f"N={w.N} steps + {levels} backward levels in FP64, whole-solve time "
                        f"extrapolated as t_fwd + N*t_level")}
+
+
+def cpu_model() -> str:
+    """Host CPU model (lscpu), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+def oracle_baseline(w: W.Workload) -> dict:
+    """The oracle on the host cores: one warm-up, then the best of 3 samples (forward sweep
+    + 1 backward level each, extrapolated as t_fwd + N t_level) with every core."""
+    oracle_sample(w, levels=1)
+    runs = [oracle_sample(w, levels=1) for _ in range(3)]
+    best = max(runs, key=lambda r: r["value"])
+    best.pop("wall_s")
+    best["sample"] += "; best of 3 after 1 warm-up"
+    best["cpu_model"] = cpu_model()
+    best["values_of_3"] = [r["value"] for r in runs]
+    return best
+
+
+def start_single_thread_baseline(w: W.Workload):
+    """The same oracle sample with one thread, in a background process (its result is read
+    by finish_single_thread_baseline)."""
+    out = tempfile.mktemp(prefix="oracle1_", suffix=".json")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "from paper_2510_02635_gb300 import workloads as W; "
+            "r = bench.oracle_sample(W.ALL[%r], levels=1); r.pop('wall_s'); "
+            "json.dump(r, open(%r, 'w'))" % (ROOT, w.name, out))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    return subprocess.Popen([sys.executable, "-c", code], env=env,
+                            stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL), out
+
+
+def finish_single_thread_baseline(handle, timeout: float = 600.0) -> dict | None:
+    proc, out = handle
+    try:
+        proc.wait(timeout=timeout)
+        r = json.load(open(out))
+        return {"value": r["value"], "cores": 1, "level_s": r["level_s"],
+                "forward_s": r["forward_s"], "sample": r["sample"] + " (one run)"}
+    except (subprocess.TimeoutExpired, OSError, ValueError):
+        proc.kill()
+        return None
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -260,6 +370,33 @@ def extra_batched(sample: int = 32) -> dict:
                                    "worst_M_over_d": max(errs, key=lambda e: max(e[0], e[1]))[2]}}}
 
 
+def extra_batched_sharded(rank: int, world: int, dist) -> dict:
+    """Multi-GPU: the 512-instance uneven batch split over the ranks by estimated cost
+    (shard.cost_shard, no collective on the data path); each rank launches its share as one
+    autotuned plan; the batch time is the maximum over ranks."""
+    import torch
+
+    from paper_2510_02635_gb300 import autotune, shard
+    inst = autotune.route_precision(W.batch_instances())
+    x0s = W.batch_x0(inst)
+    mine = shard.cost_shard(inst, world)[rank]
+    sub = [inst[i] for i in mine]
+    # each rank tunes its own buckets without the shared cache file (no concurrent writers)
+    batch = autotune.Batch(sub, [x0s[i] for i in mine], autotune.tune(sub, cache_path=None))
+    dist.barrier()
+    ms = _events_ms(batch.launch, 2)
+    status = int(batch.plan.diagnostics().status)
+    batch.close()
+    t = torch.tensor([ms], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = sum(w.M * w.d * w.N for w in inst)
+    return {"workload": W.BATCH_NAME, "instances": len(inst), "ranks": world,
+            "instances_this_rank": len(sub), "ms_per_batch_max_over_ranks": ms_max,
+            "value": units / (ms_max * 1e-3), "unit": UNIT, "device_status_rank0": status,
+            "split": "cost_shard (largest estimated cost first onto the least loaded rank)"}
+
+
 def extra_adjoint() -> dict:
     """The reverse sweep (d u / d x0, d u / d theta) of the log-quadratic workload vs its
     primal solve, both eager, CUDA events."""
@@ -291,8 +428,10 @@ def extra_anchored() -> dict:
     u = torch.empty(1, dtype=torch.float64, device="cuda")
     g = torch.empty(1, w.d, dtype=torch.float64, device="cuda")
 
+    status = [0]
+
     def run():
-        fbsde.fbsde_solve_anchored(p, 1, x0, w.seed, 0, u, g, ws)
+        status[0] = fbsde.fbsde_solve_anchored(p, 1, x0, w.seed, 0, u, g, ws)
 
     ms = _events_ms(run, 3)
     u_anchored = float(u[0])
@@ -301,25 +440,39 @@ def extra_anchored() -> dict:
     u_single = float(single.solve(x0, seed=w.seed)["u0"][0])
     exact = math.exp(-w.T) * 1.0   # mean of cos 0
     out = {"workload": "ac_manufactured_d100_M2048_N10_Q1_fp32_per_anchor", "ms_per_solve": ms,
-           "unit_note": "M^2 d N anchor-particle-dims per solve",
-           "value": w.M * w.M * w.d * w.N / (ms * 1e-3),
-           "u0": u_anchored, "u0_single_anchor": u_single, "u0_exact": exact,
-           "abs_err": abs(u_anchored - exact), "abs_err_single_anchor": abs(u_single - exact)}
+           "status": status[0], "unit_note": "M^2 d N anchor-particle-dims per solve",
+           "u0_single_anchor": u_single, "u0_exact": exact,
+           "abs_err_single_anchor": abs(u_single - exact)}
+    if status[0] == 0:   # a failed solve reports its status only
+        out.update(value=w.M * w.M * w.d * w.N / (ms * 1e-3), u0=u_anchored,
+                   abs_err=abs(u_anchored - exact))
     # the same solve with each anchor's regression over a batch of K particles (the
-    # random-batch reading of Remark 2.1); the products still run over all M particles
+    # batch reading of Remark 2.1: cyclic windows, products restricted to their band), at
+    # M = 2048 and M = 4096: the cost per level grows like M (K + 128) d, not M^2 d
     K = 256
-    try:
-        status = [0]
+    out["batch"] = []
+    for Mb in (w.M, 2 * w.M):
+        try:
+            pb = fbsde.make_problem(w.kind, w.d, w.N, Mb, w.sigma, w.T, w.precision, h=w.h,
+                                    ridge_rel=w.ridge_rel, cg_tol=w.cg_tol)
+            wsb = ws if Mb == w.M else torch.empty(fbsde.fbsde_anchored_workspace_bytes(pb),
+                                                   dtype=torch.uint8, device="cuda")
+            st_b = [0]
 
-        def run_batch():
-            status[0] = fbsde.fbsde_solve_batch(p, K, 1, x0, w.seed, 0, u, g, ws)
+            def run_batch():
+                st_b[0] = fbsde.fbsde_solve_batch(pb, K, 1, x0, w.seed, 0, u, g, wsb)
 
-        ms_b = _events_ms(run_batch, 3)
-        u_b = float(u[0])
-        out["batch"] = {"K": K, "ms_per_solve": ms_b, "status": status[0], "u0": u_b,
-                        "abs_err": abs(u_b - exact)}
-    except Exception as e:   # reported in the line, never fatal to the bench
-        out["batch"] = {"K": K, "error": repr(e)}
+            ms_b = _events_ms(run_batch, 3)
+            u_b = float(u[0])
+            rec = {"K": K, "M": Mb, "ms_per_solve": ms_b, "status": st_b[0]}
+            if st_b[0] == 0:
+                rec.update(u0=u_b, abs_err=abs(u_b - exact))
+            out["batch"].append(rec)
+            del wsb
+        except Exception as e:   # reported in the line, never fatal to the bench
+            out["batch"].append({"K": K, "M": Mb, "error": repr(e)})
+    if out["batch"] and "ms_per_solve" in out["batch"][0]:
+        out["batch_speedup_vs_all_particles"] = ms / out["batch"][0]["ms_per_solve"]
     return out
 
 
@@ -369,7 +522,7 @@ def run_gpu(args, rank: int, world: int) -> None:
         grad = torch.empty(w.Q, w.d, dtype=torch.float64, device="cuda")
         fbsde.check(fbsde.fbsde_solve(solver.problem, w.Q, x0, w.seed, sidx, out, grad,
                                       solver.workspace), "fbsde_solve")
-        return out
+        return out, grad
 
     for _ in range(args.warmup):
         step()
@@ -379,7 +532,7 @@ def run_gpu(args, rank: int, world: int) -> None:
     # library's launch profiler brackets only the matrix-free product (the roofline
     # kernel) with events, so its own event records stay out of the other kernels
     fbsde.fbsde_profile_start(1 << 20)
-    fbsde.fbsde_profile_select(["matvec"])
+    fbsde.fbsde_profile_select(["matvec", "step"])
     with ClockSampler(_gpu_uuid(torch)) as clk:
         if dist:
             dist.barrier()
@@ -387,7 +540,7 @@ def run_gpu(args, rank: int, world: int) -> None:
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            u = step()
+            u, g = step()
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -421,6 +574,12 @@ def run_gpu(args, rank: int, world: int) -> None:
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
+    # the fused per-level step (row read + write, 8 B per particle-dim; the forward sweep's
+    # end point writes only, 4 B), timed inside the same region
+    st_k = prof["step"]
+    step_ms = st_k["total_ms"] / args.steps
+    step_bytes = 8.0 * w.Q * w.M * w.d * (w.N - 1) + 4.0 * w.Q * w.M * w.d
+    step_gbs = step_bytes / (step_ms * 1e-3) / 1e9
     # kernels the library launched one by one, plus those run inside the CG-loop graphs
     # (one reset kernel per level and three per pass beyond the eager ones)
     beyond = np.maximum(cg_iters.reshape(w.Q, w.N).max(axis=0) - eager, 0)
@@ -460,17 +619,23 @@ def run_gpu(args, rank: int, world: int) -> None:
         e2e_s = float(t.item())
     e2e_value = units / e2e_s
 
-    cpu = None
+    cpu, single = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(w, levels=2)
-        cpu.pop("wall_s")
+        cpu = oracle_baseline(w)
+        single = start_single_thread_baseline(w)   # runs while the GPU extras run
     extras = {}
+    if world > 1 and not args.no_extras:
+        del ws
+        torch.cuda.empty_cache()
+        extras = {"batched_sharded": extra_batched_sharded(rank, world, dist)}
     if rank == 0 and world == 1 and not args.no_extras:
         del ws
         torch.cuda.empty_cache()
         extras = {"batched": extra_batched(), "adjoint": extra_adjoint(),
                   "logistic_d1000_plan": extra_logistic(), "per_anchor": extra_anchored()}
 
+    if single is not None:
+        cpu["single_thread"] = finish_single_thread_baseline(single)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -499,9 +664,19 @@ def run_gpu(args, rank: int, world: int) -> None:
             "kernels_ms_per_step": {k: v["total_ms"] for k, v in split.items()},
             "kernels_ms_note": "one extra solve after the timed region with every launch "
                                "bracketed by events (the timed region brackets only matvec)",
+            "roofline_step": {"kernel": "step", "bound": "hbm", "achieved": step_gbs,
+                              "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                              "frac": step_gbs / peak, "traffic": _step_traffic(w),
+                              "traffic_source": "ncu capture of the level step at Q=4, "
+                                                "M=16384 scaled per particle-dim "
+                                                "(profiles/step_traffic.txt); per solve",
+                              "algorithmic_bytes_per_solve": step_bytes,
+                              "launches_per_solve": st_k["launches"] / args.steps,
+                              "kernel_ms_per_step": step_ms},
             "cg_iters_mean": float(cg_iters.mean()), "cg_iters_max": int(cg_iters.max()),
             "device_status": status,
             "u0_sample": float(u[0]),
+            "accuracy": _accuracy(w, u.cpu().numpy(), g.cpu().numpy()),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "extras": extras,

@@ -181,7 +181,9 @@ FBSDE_API int fbsde_solve_host(const fbsde_problem *P, int32_t Q, const double *
  *   x0, u0, grad_u0 and P->theta are device pointers, as for fbsde_solve; grad_u0 may
  *   be NULL.  There is no trace output.
  * The first call on each device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream capture.
+ * device current) and caches it; make that first call before any stream capture.  The
+ * cached address is not refreshed, so calls on a device after cudaDeviceReset are not
+ * supported.
  * All calls share the one array, which keeps the last call's contents.  Each solve
  * rewrites every byte of it that it later reads, so nothing needs clearing between
  * calls, but calls whose GPU work may overlap in time (other streams, other host
@@ -218,9 +220,11 @@ FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const doub
                                    void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
 
 /* Algorithm 1 per particle anchor, each anchor's regression over a batch of K particles
- * (the random-batch reading of Remark 2.1): for anchor m the batch is the cyclic window
- * j = (m + q) mod M, q = 0..K-1.  The particle paths are independent and identically
- * distributed and the window does not depend on them, so it is a random batch in law.  The
+ * (the batch reading of Remark 2.1): for anchor m the batch is the cyclic window
+ * j = (m + q) mod M, q = 0..K-1, a window that contains the anchor's own path (q = 0)
+ * and K - 1 other paths.  The window does not depend on the positions; since the other
+ * paths are independent and identically distributed, those K - 1 particles are a random
+ * sample of the cloud, but the anchor's own path is always in its batch.  The
  * Gaussian weights, the moments and the ridge are those of fbsde_solve_anchored restricted
  * to the batch (weights normalised over it); K = M is fbsde_solve_anchored.
  *   2 <= K <= M, else FBSDE_ERR_ARG; every other argument, the workspace

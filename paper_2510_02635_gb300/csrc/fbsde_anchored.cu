@@ -50,18 +50,22 @@ struct Anchor {
 // Split K: block z sums k in [z kc, (z+1) kc) into its own output C + z Mr ldc; the
 // consumers add the splits in z order.
 // ---------------------------------------------------------------------------
+// Band (batch reading, see dev::Band): NT products skip tiles with no used entry; TN
+// products write a zero partial for a split whose rows miss the band of the tile's anchors.
 template <typename Real, bool TN>
 __global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int K, int kc,
                                               const Real *__restrict__ A, int lda,
                                               const Real *__restrict__ B, int ldb,
-                                              Real *__restrict__ C, int ldc)
+                                              Real *__restrict__ C, int ldc, dev::Band band)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ Real As[BK][BM + 1];
     __shared__ Real Bs[BK][BN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    if (!TN && !band.hits(r0, min(Mr, r0 + BM), c0, min(Nc, c0 + BN))) return;
+    if (TN && !band.hits(kb, ke, r0, min(Mr, r0 + BM))) ke = kb;   // zero partial
     C += (size_t)blockIdx.z * Mr * ldc;
     Real acc[4][4];
 #pragma unroll
@@ -237,14 +241,17 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, 
         const Real am = (Real)an[m], ref = (Real)rho_ref;
         const Real scale = p.uniform ? Real(0) : (Real)(-1.0 / (p.h2 * rho_ref));
         for (long long j = j0; j < j1; ++j) {
-            const Real rho = max((Real)pn[j] + am - Real(2) * G[(size_t)j * p.M + m], Real(0));
             long long off = j - m;   // position of particle j in anchor m's window
             if (off < 0) off += p.M;
-            const Real w = off < Kb ? exp((rho - ref) * scale) : Real(0);
+            Real w = Real(0);
+            if (off < Kb) {   // outside the window the product entry may not be computed
+                const Real rho = max((Real)pn[j] + am - Real(2) * G[(size_t)j * p.M + m], Real(0));
+                w = exp((rho - ref) * scale);
+                sw += w;
+                swy += w * (Real)Y[j];
+                swr += w * rho;
+            }
             W[(size_t)j * p.M + m] = w;
-            sw += w;
-            swy += w * (Real)Y[j];
-            swr += w * rho;
         }
         o[0] = (double)sw;
         o[1] = (double)swy;
@@ -256,7 +263,9 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, 
         Real sum = 0;
         for (long long j = j0; j < j1; ++j) {
             const size_t ix = (size_t)j * p.M + m;
-            const Real t = W[ix] * (G[ix] - ap) * inv;
+            long long off = j - m;
+            if (off < 0) off += p.M;
+            const Real t = off < Kb ? W[ix] * (G[ix] - ap) * inv : Real(0);
             T[ix] = t;
             sum += t;
         }
@@ -357,7 +366,8 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc,
 // r -= a q, p = r + (rr'/rr) p; counts the anchors still active.  G_m is the sum of the
 // nsplit partial products (split_sum).
 template <typename Real>
-__global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, int nsplit,
+__global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, int rows_per_chunk,
+                                                           dev::Band band, int nsplit,
                                                            const Real *A, const Real *G,
                                                            const double *part, const double *S,
                                                            Anchor *st, double *x, double *r,
@@ -370,7 +380,11 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
     Anchor &a = st[m];
     if (a.done) return;
     double cs[1] = {0.0};   // sum_j T_jm: lane-strided row chunks in order, then the warp tree
-    for (int c = lane; c < nrc; c += 32) cs[0] += part[((size_t)c * p.M + m) * 3];
+    for (int c = lane; c < nrc; c += 32) {   // chunks off anchor m's window hold no entry
+        const long long j0 = (long long)c * rows_per_chunk;
+        if (band.hits(j0, min((long long)p.M, j0 + rows_per_chunk), m, m + 1))
+            cs[0] += part[((size_t)c * p.M + m) * 3];
+    }
     warp_sums(cs);
     const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
     const double sp = a.sp, lam = a.lam, rr = a.rr;
@@ -641,7 +655,7 @@ inline bool tc_layout_ok(bool tn, int K, int kc, const void *A, int lda, const v
 
 template <bool TN, class Epi>
 cudaError_t gemm_tc(int Mr, int Nc, int K, int kc, const float *A, int lda, const float *B,
-                    int ldb, const Epi &epi, int *status, cudaStream_t s)
+                    int ldb, const Epi &epi, int *status, cudaStream_t s, dev::Band band)
 {
     cudaError_t e = cudaFuncSetAttribute(dev::k_gemm_tc<TN, Epi>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -650,20 +664,22 @@ cudaError_t gemm_tc(int Mr, int Nc, int K, int kc, const float *A, int lda, cons
     const dim3 grid((Nc + dev::kTcBN - 1) / dev::kTcBN, (Mr + dev::kTcBM - 1) / dev::kTcBM,
                     (K + kc - 1) / kc);
     dev::k_gemm_tc<TN, Epi><<<grid, dev::kTcThreads, dev::kTcSmemBytes, s>>>(Mr, Nc, K, kc, A, lda,
-                                                                           B, ldb, epi, status);
+                                                                           B, ldb, epi, status,
+                                                                           band);
     return cudaGetLastError();
 }
 
 template <typename Real, bool TN>
 cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Real *B, int ldb,
-                 Real *C, int ldc, int *status, cudaStream_t s)
+                 Real *C, int ldc, int *status, cudaStream_t s, dev::Band band)
 {
     if constexpr (sizeof(Real) == 4) {
         if (Mr >= 1024 && tc_layout_ok(TN, K, kc, A, lda, B, ldb))
-            return gemm_tc<TN>(Mr, Nc, K, kc, A, lda, B, ldb, dev::TcStore{C, Mr, ldc}, status, s);
+            return gemm_tc<TN>(Mr, Nc, K, kc, A, lda, B, ldb, dev::TcStore{C, Mr, ldc}, status, s,
+                               band);
     }
     const dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, (K + kc - 1) / kc);
-    k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc);
+    k_gemm<Real, TN><<<grid, 256, 0, s>>>(Mr, Nc, K, kc, A, lda, B, ldb, C, ldc, band);
     return cudaGetLastError();
 }
 
@@ -705,6 +721,10 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
     // epilogue, with column sums over 128-row tiles
     const bool fused = sizeof(Real) == 4 && M >= 1024 && tc_layout_ok(false, ld, ld, P, ld, A, ld);
     const int nrc_fused = (M + dev::kTcBM - 1) / dev::kTcBM;
+    // batch reading: the products cover only the band of entries the windows use (tiles and
+    // K-splits off it are skipped); T's entries off the band stay zero for the whole solve
+    const dev::Band band{(long long)M, Kb < M ? Kb : (long long)M};
+    if (fused && Kb < M) ANC_TRY(cudaMemsetAsync(T, 0, (size_t)M * M * sizeof(Real), s));
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
         const double a = (double)k / (double)(k + 1), b = p.sigma * std::sqrt(p.dt * a);
@@ -712,12 +732,12 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         ANC_TRY(cudaGetLastError());
         k_anc_rows<Real><<<M, 128, 0, s>>>(p, P, A, Y, pn, an, YP);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, cnt + 1, s)));   // P A^T
+        ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, A, ld, G1, M, cnt + 1, s, band)));   // P A^T
         const double rho_ref = p.sigma * p.sigma * p.d * (t_k + (k + 1) * p.dt);
         k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 0, rho_ref, Kb, G1, pn, an, Y, W, T, st, cs);
         ANC_TRY(cudaGetLastError());
-        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, cnt + 1, s)));    // W^T P
-        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, cnt + 1, s)));   // W^T (Y P)
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, cnt + 1, s, band)));    // W^T P
+        ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, cnt + 1, s, band)));   // W^T (Y P)
         k_anc_setup<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S,
                                                            rhs, x, r, pv, V);
         ANC_TRY(cudaGetLastError());
@@ -727,15 +747,16 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
             if (fused) {   // T and its column sums straight from the product's epilogue
                 if constexpr (sizeof(Real) == 4)
                     ANC_TRY((gemm_tc<false>(M, M, ld, ld, P, ld, V, ld,
-                                            TcColumnsEpi{W, T, st, cs, M}, cnt + 1, s)));
+                                            TcColumnsEpi{W, T, st, cs, M}, cnt + 1, s, band)));
             } else {
-                ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, s)));   // U = P V^T
+                ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, s, band)));   // U = P V^T
                 k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, Kb, G1, pn, an, Y, W, T, st, cs);
                 ANC_TRY(cudaGetLastError());
             }
-            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, s)));   // T^T P
+            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, s, band)));   // T^T P
             k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, s>>>(
-                p, fused ? nrc_fused : L.nrc, L.nsplit, A, G2, cs, S, st, x, r, pv, q, V, cnt);
+                p, fused ? nrc_fused : L.nrc, fused ? dev::kTcBM : kRowChunk, band, L.nsplit, A,
+                G2, cs, S, st, x, r, pv, q, V, cnt);
             ANC_TRY(cudaGetLastError());
             if (check) {
                 ANC_TRY(cudaMemcpyAsync(host_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));

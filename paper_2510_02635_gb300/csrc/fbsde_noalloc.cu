@@ -20,7 +20,9 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device.  In host code the name
 // g_noalloc_scratch is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache is not refreshed: after a
+// cudaDeviceReset the module is loaded again and the array may move, so this entry point
+// is not supported on a device after it has been reset.
 int scratch_address(void **out)
 {
     int dev = 0;

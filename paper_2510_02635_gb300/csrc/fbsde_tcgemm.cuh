@@ -155,6 +155,23 @@ __device__ __forceinline__ void tc_store(const float4 (&v)[2], uint8_t *hi, uint
     }
 }
 
+// Band of the batch reading (Remark 2.1): anchor m's regression uses the particles
+// j = (m + q) mod M, q < Kb, so only entries (j, m) with (j - m) mod M < Kb are ever used.
+// Kb >= M (or M = 0): every entry.
+struct Band {
+    long long M, Kb;
+    // true if some j in [j0, j1) and m in [m0, m1) have (j - m) mod M < Kb
+    __host__ __device__ bool hits(long long j0, long long j1, long long m0, long long m1) const
+    {
+        if (M <= 0 || Kb >= M) return true;
+        if (j1 <= j0 || m1 <= m0) return false;
+        const long long lo = j0 - (m1 - 1), hi = j1 - 1 - m0;   // offsets j - m, inclusive
+        if (hi - lo + 1 >= M) return true;
+        const long long lm = ((lo % M) + M) % M, hm = lm + (hi - lo);
+        return lm < Kb || hm >= M;
+    }
+};
+
 // Plain epilogue: C + z Mr ldc gets split z's product.
 struct TcStore {
     float *C;
@@ -184,10 +201,14 @@ struct TcStore {
 // Epi::kColSums, passed to Epi::colsum(row tile, c, sum).
 // Grid (ceil(Nc / 128), ceil(Mr / 128), splits), kTcThreads threads, kTcSmemBytes of
 // dynamic shared memory.  A wait that times out sets *status = FBSDE_ERR_TIMEOUT (if 0).
+// Band (batch reading): NT products (rows j, columns m) skip tiles that hold no used entry,
+// writing nothing (the consumers read only entries in the band, or zero them beforehand);
+// TN products (rows m, contraction over j) treat a split whose rows j miss the band of the
+// tile's anchors as empty, so the epilogue writes its zero partial.
 template <bool TN, class Epi>
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_gemm_tc(int Mr, int Nc, int K, int kc, const float *__restrict__ A, int lda,
-              const float *__restrict__ B, int ldb, Epi epi, int *status)
+              const float *__restrict__ B, int ldb, Epi epi, int *status, Band band)
 {
     extern __shared__ __align__(1024) uint8_t tsm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + kTcStages * kTcStageBytes);
@@ -195,7 +216,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.y * kTcBM, c0 = blockIdx.x * kTcBN;
     const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
-    const int nk = ke > kb ? (ke - kb + kTcBK - 1) / kTcBK : 0;
+    if (!TN && !band.hits(r0, min(Mr, r0 + kTcBM), c0, min(Nc, c0 + kTcBN))) return;
+    const bool used = !TN || band.hits(kb, ke, r0, min(Mr, r0 + kTcBM));
+    const int nk = (used && ke > kb) ? (ke - kb + kTcBK - 1) / kTcBK : 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(

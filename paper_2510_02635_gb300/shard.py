@@ -1,8 +1,12 @@
-"""Multi-GPU decomposition of the hot path: query points are independent solves, so they
-shard across ranks with no collective on the data path.  Two host-side helpers ride on
-torch.distributed: the step time reduced as the maximum over ranks, and an optional
-gather of the per-query results (d + 1 numbers per query) onto every rank."""
+"""Multi-GPU decomposition of the hot path: query points and batch instances are
+independent solves, so they shard across ranks with no collective on the data path.
+Query points of one problem split into equal contiguous blocks (query_shard); the uneven
+instances of a batch split by their estimated cost (cost_shard: largest first onto the
+least loaded rank).  Host-side helpers ride on torch.distributed: the step time reduced as
+the maximum over ranks, and gathers of the per-query or per-instance results."""
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -46,3 +50,47 @@ def gather_queries(local: np.ndarray, q_total: int, device="cpu") -> np.ndarray:
     rows = [p[:c].cpu().numpy() for p, c in zip(parts, counts)]
     out = np.concatenate(rows, axis=0)
     return out.reshape((q_total,) + local.shape[1:])
+
+
+def instance_cost(w) -> float:
+    """Estimated work of one instance: Q M d N particle-dims per pass times the passes per
+    level, 2 + sqrt(kappa) (the row step and the moments, then CG passes growing like the
+    square root of the regression's condition number kappa, estimated from the
+    Marchenko-Pastur edges of the cloud's covariance and the ridge).  The plan's branch
+    scheduler uses a model of the same form."""
+    from .autotune import kappa_estimate
+    return float(w.Q) * w.M * w.d * w.N * (2.0 + math.sqrt(kappa_estimate(w)))
+
+
+def cost_shard(instances, world: int) -> list[list[int]]:
+    """Instance indices per rank: largest estimated cost first, each onto the rank with the
+    least total so far (ties: the lower rank; equal costs keep instance order), every list
+    in increasing index order.  Deterministic, so every rank computes the same split."""
+    if world < 1:
+        raise ValueError("bad shard arguments")
+    costs = [instance_cost(w) for w in instances]
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts: list[list[int]] = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def gather_instances(local: dict, n_total: int) -> list:
+    """Every rank's {instance index: result} merged onto every rank, as a list in instance
+    order (results of uneven size, e.g. (u0, grad u) with each instance's own d)."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        merged = dict(local)
+    else:
+        parts = [None] * dist.get_world_size()
+        dist.all_gather_object(parts, local)
+        merged = {}
+        for part in parts:
+            merged.update(part)
+    if sorted(merged) != list(range(n_total)):
+        raise ValueError("the shards do not cover every instance exactly once")
+    return [merged[i] for i in range(n_total)]

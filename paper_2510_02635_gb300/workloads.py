@@ -72,6 +72,23 @@ def inputs(w: Workload) -> dict:
     return {"x0": np.ascontiguousarray(x0), "theta": theta}
 
 
+def exact_solution(w: Workload, x0) -> tuple[float, np.ndarray] | None:
+    """u(0, x0) and grad u(0, x0) of the workload's manufactured closed form, or None for
+    kinds without one.  These are properties of the test problems (checked against the PDE
+    (2.1) symbolically by the oracle tests), not arithmetic of the scheme:
+      Allen-Cahn with manufactured source: u = e^{t - T} (1/d) sum_i cos x_i;
+      gradient-dependent logistic driver (sigma = d): u = 1 / (1 + exp(-(t + sum_i x_i / d))).
+    """
+    x0 = np.asarray(x0, dtype=np.float64)
+    if w.kind == "ac_manufactured":
+        e = math.exp(-w.T)
+        return e * float(np.mean(np.cos(x0))), -e * np.sin(x0) / w.d
+    if w.kind == "logistic_grad" and w.sigma == float(w.d):
+        u = 1.0 / (1.0 + math.exp(-float(np.sum(x0)) / w.d))
+        return u, np.full(w.d, u * (1.0 - u) / w.d)
+    return None
+
+
 # Plain scheme at d = 100, FP64 throughout (Allen-Cahn with manufactured source).
 C0_AC_D100 = Workload("ac_manufactured_d100_M2048_N10_Q1_fp64", "ac_manufactured", d=100,
                       sigma=1.0, T=0.5, N=10, M=2048, Q=1, seed=0, x0_law="zero",

@@ -40,7 +40,7 @@ cudaError_t launch(const Case &c, const float *A, int lda, const float *B, int l
     if (e != cudaSuccess) return e;
     const dim3 grid((c.Nc + 127) / 128, (c.Mr + 127) / 128, (c.K + c.kc - 1) / c.kc);
     k_gemm_tc<TN, TcStore><<<grid, kTcThreads, kTcSmemBytes>>>(c.Mr, c.Nc, c.K, c.kc, A, lda, B,
-                                                              ldb, TcStore{C, c.Mr, ldc}, st);
+                                                              ldb, TcStore{C, c.Mr, ldc}, st, fbsde::dev::Band{0, 0});
     return cudaGetLastError();
 }
 

@@ -101,3 +101,40 @@ def test_autograd_function_matches_reverse_sweep():
     adj = solver.adjoint(inp["x0"], seed=w.seed, u0_bar=[0.5, 1.0, -2.0], with_theta=True)
     assert torch.allclose(x0.grad, adj["x0_bar"], rtol=0, atol=0)
     assert torch.allclose(theta.grad, adj["theta_bar"], rtol=0, atol=0)
+
+
+def test_adjoint_and_regression_gradient_estimate_the_same_grad_u():
+    """Two estimators of grad u(0, x0) from one solve: the reverse sweep's du/dx0 (the
+    derivative of the estimator u(0, x0) for fixed increments) and the scheme's own
+    regression slope alpha_x of level 0 (Algorithm 1's grad u output).  On the adjoint
+    workload (log-quadratic terminal, d = 1000, M = 4096, N = 20, FP32) one call solves the
+    same x0 with 16 independent Philox streams.  The regression slope is far noisier than
+    the reverse sweep, so they are compared statistically:
+      - along the direction of the mean of du/dx0, the means over the streams agree within
+        4 standard errors of their difference;
+      - over all d components, the per-component t statistic of the mean difference has
+        mean square at most the t distribution's (n - 1)/(n - 3) plus 5 of its standard
+        deviations over d independent components (doubled for their correlation)."""
+    n = 16
+    base = W.C4_HJB_D1000
+    w = base.with_(Q=n)
+    inp = W.inputs(base)
+    x0 = np.repeat(inp["x0"][:1], n, axis=0)
+    out = _solver(w, inp["theta"]).adjoint(x0, seed=w.seed)
+    assert out["status"] == 0
+    A = out["x0_bar"].cpu().numpy()
+    G = out["grad"].cpu().numpy()
+    a = A.mean(axis=0)
+    ahat = a / np.linalg.norm(a)
+    pa, pg = A @ ahat, G @ ahat
+    se = math.sqrt(pa.var(ddof=1) / n + pg.var(ddof=1) / n)
+    assert abs(pg.mean() - pa.mean()) <= 4.0 * se, (pg.mean(), pa.mean(), se)
+    D = G - A
+    t = D.mean(axis=0) / (D.std(axis=0, ddof=1) / math.sqrt(n))
+    nu = n - 1
+    mean_t2 = nu / (nu - 2)
+    sd_t2 = math.sqrt(2 * nu ** 2 * (nu - 1) / ((nu - 2) ** 2 * (nu - 4)) / w.d)
+    assert float(np.mean(t * t)) <= mean_t2 + 10.0 * sd_t2, float(np.mean(t * t))
+    # the reverse sweep itself is precise: its spread over the streams along its mean is
+    # a small fraction of |grad u|
+    assert pa.std(ddof=1) <= 0.2 * np.linalg.norm(a)

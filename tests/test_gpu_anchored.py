@@ -148,3 +148,15 @@ def test_batch_on_the_tensor_core_path_matches_oracle():
     from paper_2510_02635_gb300 import fbsde as fb
     out, refs, *_ = _run(fb, "ac_manufactured", 21, 1030, 2, "fp32", {}, Q=1, K=300)
     _check(out, refs, TOL_FP32)
+
+
+@pytest.mark.parametrize("prec,tol,M,K", [("fp64", TOL_FP64, 700, 50), ("fp32", TOL_FP32, 700, 50),
+                                          ("fp32", TOL_FP32, 1300, 40)])
+def test_banded_products_match_oracle(prec, tol, M, K):
+    """Narrow windows (K << M): the products cover only the band of (particle, anchor)
+    entries the windows use, skipping most tiles of the M x M products and most K-splits
+    of the tall ones (SIMT tiles at M = 700, tensor-core tiles at M = 1300; the band wraps
+    around the last anchors).  Same bar as the full batch solve."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, "ac_manufactured", 24, M, 2, prec, {}, Q=1, K=K)
+    _check(out, refs, tol)

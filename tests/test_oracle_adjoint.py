@@ -150,3 +150,39 @@ def test_adjoint_solution_moves_between_levels(kind, d, M, sigma, T):
     prim = oracle.solve(p, x0, 4, 0, trace=True)["alpha_x"]
     steady = [np.linalg.norm(prim[k] - prim[k + 1]) / np.linalg.norm(prim[k]) for k in range(N - 1)]
     assert np.median(steady) < np.median(const)
+
+
+def test_adjoint_derivatives_against_cole_hopf_monte_carlo():
+    """sigma = sqrt 2, f = -|z|^2/2, g = log((1 + sum theta_i x_i^2)/2): v = e^{-u} solves the
+    heat equation, so u(0,x0) = -ln E[e^{-g(X_T)}], X_T = x0 + sqrt 2 W_T, and its
+    derivatives are ratios of expectations,
+        du/dx0_i   = E[e^{-g} 2 theta_i X_i / (1 + sum theta X^2)] / E[e^{-g}],
+        du/dtheta_i = E[e^{-g} X_i^2 / (1 + sum theta X^2)] / E[e^{-g}],
+    which plain Monte Carlo estimates independently of the scheme (800k samples).  The
+    oracle's reverse sweep differentiates the scheme's estimator for fixed increments; on
+    average over its cloud that is the derivative of u, so both must agree up to the
+    scheme's error (time step, regression) and the Monte-Carlo spread of each side."""
+    rng = np.random.default_rng(13)
+    d, T = 200, 1.0
+    theta = rng.uniform(0.5, 1.5, d)
+    x0 = rng.standard_normal(d) / math.sqrt(d)
+    num_x, num_t, den = np.zeros(d), np.zeros(d), 0.0
+    for _ in range(8):
+        X = x0 + math.sqrt(2.0 * T) * rng.standard_normal((100_000, d))
+        q = 1.0 + (theta * X * X).sum(axis=1)
+        v = 2.0 / q
+        den += v.sum()
+        num_x += ((v / q)[:, None] * (2.0 * theta * X)).sum(axis=0)
+        num_t += ((v / q)[:, None] * (X * X)).sum(axis=0)
+    ref_x, ref_t = num_x / den, num_t / den
+    p = oracle.Problem("hjb_logquad", d, math.sqrt(2.0), T, 10, 4096, theta=theta)
+    r = oracle.adjoint(p, x0, seed=9)
+    assert r["status"] == 0
+    err_x = np.linalg.norm(r["du_dx0"] - ref_x) / np.linalg.norm(ref_x)
+    err_t = np.linalg.norm(r["du_dtheta"] - ref_t) / np.linalg.norm(ref_t)
+    # measured (seeds 9-11): err_t 0.020-0.023 and err_x 0.069-0.072, with Monte-Carlo
+    # standard errors of the reference of 0.0015 and 0.021; a sign or factor error in
+    # either derivative lands near 1 or 2
+    assert err_t < 0.04, err_t
+    assert err_x < 0.12, err_x
+    assert 0.9 < float(r["du_dx0"] @ ref_x) / float(ref_x @ ref_x) < 1.1

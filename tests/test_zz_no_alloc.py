@@ -46,6 +46,27 @@ def test_noalloc_matches_workspace_entry_point_twice(prec, tol):
             assert np.all(np.linalg.norm(g - g_ref, axis=1) <= tol * scale)
 
 
+def test_noalloc_call_allocates_no_device_memory():
+    """The defining property: once the library's module is loaded on the device (the
+    first call does that, and looks up the scratch array's address), a call leaves the
+    device's free memory exactly where it was."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    d, N, M, Q, seed = 300, 4, 2000, 2, 5
+    rng = np.random.default_rng(6)
+    x0 = torch.tensor(rng.standard_normal((Q, d)) / math.sqrt(d), device="cuda")
+    u = torch.empty(Q, dtype=torch.float64, device="cuda")
+    g = torch.empty(Q, d, dtype=torch.float64, device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, "fp32", cg_tol=1e-8)
+    fb.check(fb.fbsde_solve_noalloc(p, Q, x0, seed, 0, u, g), "fbsde_solve_noalloc")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        fb.check(fb.fbsde_solve_noalloc(p, Q, x0, seed, 0, u, g), "fbsde_solve_noalloc")
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    assert bool(torch.isfinite(u).all())
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     from paper_2510_02635_gb300 import fbsde as fb
     p = fb.make_problem("ac_manufactured", 4000, 5, 8192, 1.0, 0.5, "fp32")
