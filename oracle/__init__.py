@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fbsde_oracle.c")
+_SRC_SDE = os.path.join(_HERE, "fbsde_oracle_sde.c")   # the scheme with a drift (same library)
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -35,6 +36,8 @@ KINDS = {
     "cubic_test": 4,
     "ac_doublewell": 5,
     "cos_linear_test": 6,
+    "drift_ac": 7,
+    "drift_quad": 8,
 }
 STATUS = {0: "ok", 1: "bad argument", 4: "newton not converged", 5: "cg not converged",
           7: "non-finite result", 8: "out of memory"}
@@ -44,11 +47,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC_SDE))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
-           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+           "-ffp-contract=off", _SRC, _SRC_SDE, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -121,6 +125,14 @@ def _load():
             lib.orc_f_grads.restype = None
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = C.c_int
+            lib.orc_solve_sde.argtypes = [C.POINTER(_Problem), C.c_void_p, _dp, C.c_uint64,
+                                          C.c_uint32, _dp, _dp, _dp, _dp, _ip, _dp]
+            lib.orc_solve_sde.restype = C.c_int
+            lib.orc_sde_g.argtypes = [C.POINTER(_Problem), _dp]
+            lib.orc_sde_g.restype = C.c_double
+            lib.orc_sde_f.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_double, _dp, C.c_double,
+                                      _dp, _dp]
+            lib.orc_sde_f.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -286,6 +298,59 @@ def solve(prob: Problem, x0, seed: int, solve_index: int = 0, max_levels: int | 
     if keep_levels_y:
         out.update(Y_levels=y_lv)
     return out
+
+
+class _SdeCoef(C.Structure):
+    _fields_ = [("mu0", C.c_double), ("mu1", C.c_double), ("sig1", C.c_double)]
+
+
+def solve_sde(prob: Problem, x0, seed: int, solve_index: int = 0, mu0: float = 0.0,
+              mu1: float = 0.0, sig1: float = 0.0, trace: bool = False,
+              keep_paths: bool = False) -> dict:
+    """Algorithm 1 with the drift mu_i(x) = mu0 + mu1 x_i and the diffusion
+    sigma(x) = diag(prob.sigma + sig1 x_i) (the forward SDE of Sec. 2.1, Euler-Maruyama
+    paths (2.7), anchor on the drift path of x0, Z = sigma(X)^T alpha_x per particle):
+    u0, grad, status and, on request, the per-level alpha, alpha_x, CG iterations and the
+    paths X_0..X_N [N+1, M, d]."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    assert x0.shape == (prob.d,)
+    N, M, d = prob.N, prob.M, prob.d
+    u0 = C.c_double(math.nan)
+    grad = np.zeros(d)
+    a_lv = np.full(N, np.nan) if trace else None
+    ax_lv = np.full((N, d), np.nan) if trace else None
+    cg_lv = np.zeros(N, dtype=np.int32) if trace else None
+    xs = np.zeros((N + 1, M, d)) if keep_paths else None
+    ps = prob.c_struct()
+    coef = _SdeCoef(float(mu0), float(mu1), float(sig1))
+    st = _load().orc_solve_sde(C.byref(ps), C.byref(coef), _ptr(x0), int(seed), int(solve_index),
+                               C.byref(u0), _ptr(grad), _ptr(a_lv), _ptr(ax_lv), _ptr(cg_lv, _ip),
+                               _ptr(xs))
+    out = {"u0": float(u0.value), "grad": grad, "status": int(st)}
+    if trace:
+        out.update(alpha=a_lv, alpha_x=ax_lv, cg_iters=cg_lv)
+    if keep_paths:
+        out["paths"] = xs
+    return out
+
+
+def sde_g(prob: Problem, x) -> float:
+    """g of the problem table of the scheme with a drift (kinds 7, 8 and the driftless ones)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_load().orc_sde_g(C.byref(prob.c_struct()), _ptr(x)))
+
+
+def sde_f(prob: Problem, t: float, x, y: float, z, mu0: float = 0.0, mu1: float = 0.0,
+          sig1: float = 0.0) -> tuple[float, float]:
+    """f(t, x, y, z) and df/dy of the scheme with a drift (the coefficients enter the
+    manufactured sources of kinds 7 and 8)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    dfdy = C.c_double()
+    coef = _SdeCoef(float(mu0), float(mu1), float(sig1))
+    v = _load().orc_sde_f(C.byref(prob.c_struct()), C.byref(coef), float(t), _ptr(x), float(y),
+                          _ptr(z), C.byref(dfdy))
+    return float(v), float(dfdy.value)
 
 
 def solve_anchored(prob: Problem, x0, seed: int, solve_index: int = 0) -> dict:
