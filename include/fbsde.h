@@ -45,7 +45,7 @@ extern "C" {
 
 typedef struct CUstream_st *fbsde_stream_t; /* the same handle as cudaStream_t */
 
-#define FBSDE_ABI_VERSION 1
+#define FBSDE_ABI_VERSION 2
 #define FBSDE_MAX_D 16384 /* largest dimension d accepted */
 #define FBSDE_MAX_D_FP64 8192 /* largest d of the FP64 path (one 16-warp team per row) */
 
@@ -79,7 +79,15 @@ typedef enum {
     /* f = y - y^3, g = 1/(2 + 0.4 |x|^2): Sec. 4.1, case 1 (use sigma = sqrt 2). */
     FBSDE_AC_DOUBLEWELL = 5,
     /* f = c0 + c1 y, g = (1/d) sum_i cos x_i. */
-    FBSDE_COS_LINEAR_TEST = 6
+    FBSDE_COS_LINEAR_TEST = 6,
+    /* For the forward SDE with drift and state-dependent diffusion (see fbsde_problem), with
+       s_i = sigma + sig1 x_i, m_i = mu0 + mu1 x_i: g = (1/d) sum_i cos x_i, f = y - y^3 + q,
+       q = u*^3 - 2 u* + e^{t-T} (1/d) sum_i [s_i^2 cos x_i / 2 + m_i sin x_i]; exact
+       solution u*(t,x) = e^{t-T} (1/d) sum_i cos x_i for any such coefficients. */
+    FBSDE_DRIFT_AC = 7,
+    /* The same with g = (1/d) sum_i x_i^2, q = u*^3 - 2 u* - e^{t-T} (1/d) sum_i
+       [s_i^2 + 2 m_i x_i]; exact solution u*(t,x) = e^{t-T} (1/d) sum_i x_i^2. */
+    FBSDE_DRIFT_QUAD = 8
 } fbsde_kind;
 
 typedef enum {
@@ -111,6 +119,18 @@ typedef struct {
                                 particle clouds; results depend on it through the order of
                                 the partial sums); 0 selects 608                          */
     int32_t reserved;        /* must be 0                                               */
+    /* Forward SDE dX = mu(t,X) dt + sigma(t,X) dW of Sec. 2.1 with the componentwise affine
+       coefficients mu_i(x) = mu0 + mu1 x_i and sigma(x) = diag(sigma + sig1 x_i).  With
+       mu0 = mu1 = sig1 = 0 (and kinds 0-6) the driftless scheme: Brownian paths drawn by the
+       bridge, fused level step.  Otherwise (and always for kinds 7-8) Euler-Maruyama paths
+       (2.7), X_{k+1} = X_k + mu(X_k) dt + sigma(X_k) sqrt(dt) xi_k, kept at checkpoints
+       every s = ceil(sqrt N) levels and recomputed segment by segment on the way back; the
+       regression of level k is anchored on the drift path a_{k+1} = a_k + mu(a_k) dt of x0,
+       its kernel scale is h^2 times the cloud's mean squared distance to that anchor,
+       Z_k^j = sigma(X_k^j)^T alpha_x per particle and the prediction is taken at the
+       drifted position X_k^j + mu(X_k^j) dt.  HJB_LOGQUAD needs sig1 = 0; fbsde_adjoint and
+       the per-anchor entry points accept only the driftless scheme. */
+    double mu0, mu1, sig1;
 } fbsde_problem;
 
 /* Optional per-level outputs of a solve (all device pointers, each may be NULL).

@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libfbsde_gb300.so")
 SOURCES = ["fbsde_api.cu", "fbsde_kernels_f32.cu", "fbsde_kernels_f64.cu", "fbsde_noalloc.cu",
            "fbsde_anchored.cu"]
 HEADERS = ["fbsde_internal.cuh", "fbsde_kernels.cuh", "fbsde_launch.cuh", "fbsde_adjoint.cuh", "fbsde_matvec.cuh",
-           "fbsde_tcgemm.cuh"]
+           "fbsde_tcgemm.cuh", "fbsde_step.cuh", "fbsde_sde.cuh"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-Xptxas", "-v"]
 

@@ -522,6 +522,7 @@ bool lay(const fbsde_problem *P, Lay &L)
     if (!(P->sigma > 0.0) || !(P->T > 0.0) || !(P->cg_tol > 0.0) || !(P->ridge_rel >= 0.0))
         return false;
     if (P->cg_max_iter < 0 || P->newton_max_iter < 0) return false;
+    if (P->mu0 != 0.0 || P->mu1 != 0.0 || P->sig1 != 0.0) return false;   // driftless only
     L.d = P->d;
     L.ld = (P->d + 3) / 4 * 4;
     L.N = P->N;

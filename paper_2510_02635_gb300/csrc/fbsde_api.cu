@@ -38,7 +38,10 @@ bool choose_team(int nch, int &tw, int &vpt, int &teams)
 int check_problem(const fbsde_problem *P, int32_t Q, bool check_theta)
 {
     if (!P || Q < 1 || Q > 65535) return FBSDE_ERR_ARG;
-    if (P->kind < FBSDE_AC_MANUFACTURED || P->kind > FBSDE_COS_LINEAR_TEST) return FBSDE_ERR_ARG;
+    if (P->kind < FBSDE_AC_MANUFACTURED || P->kind > FBSDE_DRIFT_QUAD) return FBSDE_ERR_ARG;
+    if (!std::isfinite(P->mu0) || !std::isfinite(P->mu1) || !std::isfinite(P->sig1))
+        return FBSDE_ERR_ARG;
+    if (P->kind == FBSDE_HJB_LOGQUAD && P->sig1 != 0.0) return FBSDE_ERR_ARG;
     if (P->precision != FBSDE_FP32 && P->precision != FBSDE_FP64) return FBSDE_ERR_ARG;
     if (P->d < 1 || P->d > FBSDE_MAX_D) return FBSDE_ERR_ARG;
     if (P->N < 1 || P->M < 2 || P->M > (int64_t)1 << 31) return FBSDE_ERR_ARG;
@@ -51,6 +54,14 @@ int check_problem(const fbsde_problem *P, int32_t Q, bool check_theta)
         !P->theta)
         return FBSDE_ERR_ARG;
     return FBSDE_OK;
+}
+
+// The scheme with Euler-Maruyama paths (a drift or a state-dependent diffusion, or a drift
+// kind), rather than the driftless one whose Brownian paths are drawn by the bridge.
+bool is_sde(const fbsde_problem *P)
+{
+    return P->mu0 != 0.0 || P->mu1 != 0.0 || P->sig1 != 0.0 || P->kind == FBSDE_DRIFT_AC ||
+           P->kind == FBSDE_DRIFT_QUAD;
 }
 
 // Workspace layout; independent of every pointer in P.
@@ -97,7 +108,8 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     // per row), T = 480 / R threads per row in the row pass (whole warps, or half-warps at
     // R = 30), VM = ceil(nch / T) chunks per thread; column pass in row groups of
     // tpr = min(480, nch) threads; a two-slot ring of stages in shared memory
-    L.fused = P->precision == FBSDE_FP32 && L.ld <= kStepMaxLd;
+    L.sde = is_sde(P) ? 1 : 0;
+    L.fused = !L.sde && P->precision == FBSDE_FP32 && L.ld <= kStepMaxLd;
     if (L.fused) {
         constexpr int kRows[5] = {1, 3, 5, 15, 30};
         int R = 1;
@@ -163,6 +175,18 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
     L.off_vecR = take((Qs * kVecR + 1) * lds * L.real_sz);
     L.off_state = take(Qs * sizeof(SolveState));
     L.off_bpart = take(Qs * (size_t)L.nblk * kBpart * sizeof(double));
+    if (L.sde) {
+        // Euler-Maruyama rows: checkpoints at the levels s, 2s, .. below N and one segment of
+        // s - 1 levels, s = ceil(sqrt N): about 2 sqrt(N) slabs of Q M ld instead of N - 1,
+        // for one more forward step per level on the way back
+        int sq = 1;
+        while (sq * sq < P->N) ++sq;
+        L.sde_s = sq;
+        L.sde_ncp = (P->N - 1) / sq;
+        L.sde_slots = L.sde_ncp + sq - 1;
+        L.off_store = take((size_t)L.sde_slots * Qs * Ms * lds * L.real_sz);
+        L.off_anchor = take(Qs * (size_t)(P->N + 1) * lds * L.real_sz);
+    }
     L.total = off;
     // reverse sweep: tape of the primal plus three adjoint vectors per query
     L.off_tape_w = take((size_t)P->N * Qs * Ms * L.real_sz);
@@ -225,7 +249,12 @@ Params make_params(const fbsde_problem *P, const Layout &L, void *ws, uint64_t s
         p.rk1[r] = p.key1 + (uint32_t)r * 0xBB67AE85u;
     }
     p.solve0 = solve0;
+    p.sde = L.sde;
+    p.mu0 = P->mu0;
+    p.mu1 = P->mu1;
+    p.sig1 = P->sig1;
     char *base = static_cast<char *>(ws);
+    p.anchor = L.sde ? base + L.off_anchor : nullptr;
     p.delta = base + L.off_delta;
     p.Y = reinterpret_cast<double *>(base + L.off_Y);
     p.w = base + L.off_w;
@@ -466,12 +495,16 @@ template <typename Real> cudaError_t cg_loop(const Params &p, const Layout &L, c
     return cudaSuccess;
 }
 
+template <typename Real>
+cudaError_t run_sde(Params p, const Layout &L, const double *x0, const double *theta, const Rec &r);
+
 // Algorithm 1: forward sweep, then the backward levels k = N-1..0.  Each level: the CG
 // solve of its regression (moments already reduced), then, for k >= 1, the particle
 // update to level k and the moments of the level k-1 regression.
 template <typename Real>
 cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta, const Rec &r)
 {
+    if (L.sde) return run_sde<Real>(p, L, x0, theta, r);
     using LR = Launch<Real>;
     cudaError_t e;
     const cudaStream_t s = r.s;
@@ -512,6 +545,73 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
             p.newton_level = k;
             FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
         }
+    }
+    return cudaSuccess;
+}
+
+// Algorithm 1 with Euler-Maruyama paths (2.7).  The forward sweep keeps the rows of the
+// levels s, 2s, .. (checkpoints) and of the last segment; on the way back the level-k rows
+// come from a checkpoint or the segment buffer (a segment is recomputed from its checkpoint
+// when the sweep enters it) and are copied into the row buffer, so every level's kernels
+// (and the cached CG-loop graph) see the same rows pointer.  Per level k: row sums
+// (k_sde_rows), the kernel scale (k_sde_rho), the per-particle values and weights, the
+// moments and the regression set-up of level k - 1.
+template <typename Real>
+cudaError_t run_sde(Params p, const Layout &L, const double *x0, const double *theta, const Rec &r)
+{
+    using LR = Launch<Real>;
+    cudaError_t e;
+    const cudaStream_t s = r.s;
+    const int N = p.N, sq = L.sde_s;
+    const size_t slab = (size_t)L.Q * (size_t)L.M * L.ld * L.real_sz;
+    char *store = static_cast<char *>(p.delta) - L.off_delta + L.off_store;
+    // slot of a stored level 1 <= l < N: checkpoint l / sq - 1, or segment slot l % sq - 1
+    auto slot = [&](int l) -> void * {
+        const int i = l % sq == 0 ? l / sq - 1 : L.sde_ncp + l % sq - 1;
+        return store + (size_t)i * slab;
+    };
+    FBSDE_TRY(FBSDE_K_SETUP, LR::setup(p, x0, theta, s));
+    FBSDE_TRY(FBSDE_K_SETUP, LR::sde_anchor(p, L, s));
+    const void *from = nullptr;
+    for (int k = 0; k < N; ++k) {
+        void *to = k + 1 == N ? p.delta : slot(k + 1);
+        FBSDE_TRY(FBSDE_K_FORWARD, LR::sde_forward(p, L, k, from, to, s));
+        from = to;
+    }
+    int seg = (N - 1) / sq * sq;   // the segment whose levels the forward sweep left in place
+    p.level = N;
+    p.newton_level = -1;
+    FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, N, s));
+    FBSDE_TRY(FBSDE_K_PARTICLES, LR::sde_rho(p, L, s));
+    FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+    if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
+    FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+    FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+    FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 0, s));
+    for (int k = N - 1; k >= 0; --k) {
+        p.level = k;
+        if ((e = cg_loop<Real>(p, L, r)) != cudaSuccess) return e;
+        FBSDE_TRY(FBSDE_K_CG_POST, LR::cg_post(p, L, s));
+        if (k == 0) break;
+        const int b = k / sq * sq;
+        if (b != k && b != seg) {   // recompute the segment b+1 .. min(b+sq-1, N-1)
+            const void *src = b == 0 ? nullptr : slot(b);
+            for (int l = b + 1; l < std::min(b + sq, N); ++l) {
+                FBSDE_TRY(FBSDE_K_FORWARD, LR::sde_forward(p, L, l - 1, src, slot(l), s));
+                src = slot(l);
+            }
+            seg = b;
+        }
+        if ((e = cudaMemcpyAsync(p.delta, slot(k), slab, cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+            return e;
+        FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, k, s));
+        FBSDE_TRY(FBSDE_K_PARTICLES, LR::sde_rho(p, L, s));
+        FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
+        FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));
+        FBSDE_TRY(FBSDE_K_REDUCE, LR::reduce(p, L, 3, 3, 0, s));
+        p.newton_level = k;
+        FBSDE_TRY(FBSDE_K_FINALIZE, LR::moments_finalize(p, L, 1, s));
     }
     return cudaSuccess;
 }
@@ -711,6 +811,7 @@ int fbsde_adjoint(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t 
     Layout L;
     int st = check_problem(P, Q, true);
     if (st != FBSDE_OK) return st;
+    if (is_sde(P)) return FBSDE_ERR_ARG;   // the reverse sweep walks the Brownian bridge
     st = make_layout(P, Q, L);
     if (st != FBSDE_OK) return st;
     if (!x0 || !u0_bar || !u0 || !x0_bar) return FBSDE_ERR_ARG;

@@ -5,12 +5,16 @@
 //   Y      [Q][M]          double Y_k^j of the current level
 //   w      [Q][M]          Real   kernel weight of particle j in the current regression
 //   coef   [Q][M][3]       Real   moment coefficients (w, w (Y - yref), w D.x_ws)
-//   segp   [Q][M][nseg][3] Real   per-row-segment partial sums of the row kernels
+//   segp   [Q][M][nseg][6] Real   per-row-segment partial sums of the row kernels
 //   part   [Q][G][3][ld]   Real   per-CTA partial d-vectors (moments or the CG product)
-//   spart  [Q][GP][4]      double per-particle-block partial scalars
-//   vec64  [Q][7][ld]      double x (= alpha_x), r, p, S, b/rhs, q/G, x0
-//   vecR   [Q][3][ld]      Real   p, x, x0 rounded to the stream precision; then theta [ld]
+//   spart  [Q][GS][4]      double per-particle-block partial scalars
+//   vec64  [Q][9][ld]      double x (= alpha_x), r, p, S, b/rhs, q/G, x0, s, previous alpha_x
+//   vecR   [Q][4][ld]      Real   p, alpha_x, x0, next starting guess (stream precision);
+//                                 then theta [ld]
 //   state  [Q]             SolveState
+// and, for a forward SDE with a drift or a state-dependent diffusion only:
+//   store  [slots][Q][M][ld] Real stored levels of the rows (checkpoints, one segment)
+//   anchor [Q][N+1][ld]    Real   offsets c_k = a_k - x0 of the drift path of x0
 // ld = d rounded up to a multiple of 4 (16-byte rows for float and 32-byte rows for
 // double); the padding of every row and vector is kept at zero.
 #pragma once
@@ -36,7 +40,8 @@ constexpr int kVec64 = 9;
 constexpr int kRedTile = 128;  // elements per block of the partial reduction and CG update
 constexpr int kBpart = 4;      // per-block shares: w . r, S . r, r . r, spare
 constexpr int kVecR = 4;
-constexpr int kSegSums = 4;   // per-row-segment sums of the row kernels
+constexpr int kSegSums = 6;   // per-row-segment sums of the row kernels (the forward SDE's
+                              // rows use all six, the driftless ones the first four)
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
 constexpr int kMinRowsPerCta = 8;
@@ -50,6 +55,9 @@ struct SolveState {
     double rr_prev, cg_alpha;       // previous r . r and step of the CG recurrence
     double cg_beta, cg_step;        // scalars of the current CG pass
     double sx;                      // S . x of the adjoint solve's starting guess
+    double rho_ref;                 // forward SDE: mean squared distance to the anchor
+    double sum_ax, ax_x0;           // forward SDE: sum_i alpha_x,i and alpha_x . x0
+    double psi0;                    // forward SDE: second feature of f at x0 (kinds 7, 8)
     int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive,
         arrive_q, cg_ok, pad4;
 };
@@ -62,6 +70,10 @@ struct Layout {
     // fused per-level step (FP32 rows of at most kStepMaxLd floats): rows per stage, threads
     // per row, chunks per thread in the row pass, column-pass row groups, shared memory
     int fused, st_R, st_T, st_vm1, st_tpr, st_RG, st_vm3, st_vm, st_nslot, GS, Gs;
+    // forward SDE with drift / state-dependent diffusion: checkpoint interval s, checkpoint
+    // slabs, slabs in all (checkpoints, then one segment), stored rows and anchor offsets
+    int sde, sde_s, sde_ncp, sde_slots;
+    size_t off_store, off_anchor;
     size_t st_region, st_smem;
     int64_t M;
     size_t real_sz;
@@ -82,6 +94,11 @@ struct Params {
                                                                     // nsp = spart blocks of a level
     long long st_region;  // floats of the fused step's row-slot region
     uint32_t rk0[10], rk1[10];  // Philox4x32-10 round keys of (key0, key1)
+    // forward SDE: mu_i(x) = mu0 + mu1 x_i, sigma_ii(x) = sigma + sig1 x_i; anchor offsets
+    // c_k = a_k - x0 [Q][N+1][ld] (stream precision)
+    int sde;
+    double mu0, mu1, sig1;
+    void *anchor;
     uint32_t key0, key1, solve0;
     // workspace
     void *delta;
@@ -113,6 +130,12 @@ template <typename Real> struct Launch {
     static cudaError_t particles(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t moments(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t step(const Params &p, const Layout &L, cudaStream_t s);
+    // forward SDE (fbsde_sde.cuh)
+    static cudaError_t sde_anchor(const Params &p, const Layout &L, cudaStream_t s);
+    static cudaError_t sde_forward(const Params &p, const Layout &L, int k, const void *from,
+                                   void *to, cudaStream_t s);
+    static cudaError_t sde_rows(const Params &p, const Layout &L, int k, cudaStream_t s);
+    static cudaError_t sde_rho(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t reduce(const Params &p, const Layout &L, int nvec, int dst0, int skip_done,
                               cudaStream_t s);
     static cudaError_t matvec(const Params &p, const Layout &L, cudaStream_t s);

@@ -307,6 +307,15 @@ __device__ __forceinline__ float cos_stream(float x)
     return __cosf(r);
 }
 __device__ __forceinline__ double cos_stream(double x) { return cos(x); }
+// sin with the same reduction (the drift kinds' source terms).
+__device__ __forceinline__ float sin_stream(float x)
+{
+    const float n = rintf(x * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, x);
+    r = fmaf(-n, 1.9353071795864769e-3f, r);
+    return __sinf(r);
+}
+__device__ __forceinline__ double sin_stream(double x) { return sin(x); }
 
 // Per-element term of the terminal feature sum; x = x0_i + Delta_i.
 template <typename Real> __device__ __forceinline__ Real g_term(int kind, Real x, Real th)
@@ -333,19 +342,32 @@ __device__ __forceinline__ double g_value(const Params &p, double phi)
     case FBSDE_AFFINE_TEST: return p.A + phi;
     case FBSDE_CUBIC_TEST: return p.A;
     case FBSDE_AC_DOUBLEWELL: return 1.0 / (2.0 + 0.4 * phi);
+    case FBSDE_DRIFT_AC:
+    case FBSDE_DRIFT_QUAD: return phi / p.d;
     }
     return NAN;
 }
 
 // The y-independent part of f at time t: AC_MANUFACTURED uses phi = sum_i cos x_i,
-// the z-dependent kinds use sum_i z_i and |z|^2 of the level.
+// the z-dependent kinds use sum_i z_i and |z|^2 of the level, the drift kinds the sums
+// phi (of g's terms) and psi of their source:
+//   DRIFT_AC:   u*^3 - 2 u* + e^{t-T} psi / d,  psi = sum_i s_i^2 cos x_i / 2 + m_i sin x_i;
+//   DRIFT_QUAD: u*^3 - 2 u* - e^{t-T} psi / d,  psi = sum_i s_i^2 + 2 m_i x_i;
+// u* = e^{t-T} phi / d, s_i = sigma + sig1 x_i, m_i = mu0 + mu1 x_i (these sources make u*
+// the exact solution of (2.1) under the drift mu and the diffusion diag(s)).
 __device__ __forceinline__ double f_feature(const Params &p, double t, double phi, double sumz,
-                                            double zz)
+                                            double zz, double psi = 0.0)
 {
     switch (p.kind) {
     case FBSDE_AC_MANUFACTURED: {
         const double us = exp(t - p.T) * phi / p.d;
         return us * us * us - (2.0 - 0.5 * p.sigma * p.sigma) * us;
+    }
+    case FBSDE_DRIFT_AC:
+    case FBSDE_DRIFT_QUAD: {
+        const double e = exp(t - p.T), us = e * phi / p.d;
+        const double q = e * psi / p.d;
+        return us * us * us - 2.0 * us + (p.kind == FBSDE_DRIFT_AC ? q : -q);
     }
     case FBSDE_LOGISTIC_GRAD: return sumz;
     case FBSDE_HJB_LOGQUAD: return zz;
@@ -358,6 +380,8 @@ __device__ __forceinline__ double f_scalar(const Params &p, double feat, double 
 {
     switch (p.kind) {
     case FBSDE_AC_MANUFACTURED:
+    case FBSDE_DRIFT_AC:
+    case FBSDE_DRIFT_QUAD:
         dfdy = 1.0 - 3.0 * y * y;
         return y - y * y * y + feat;
     case FBSDE_LOGISTIC_GRAD:
@@ -460,6 +484,11 @@ template <typename Real> struct WS {
     __device__ __forceinline__ Real *thetaR() const
     {
         return reinterpret_cast<Real *>(p.vecR) + (size_t)p.Q * kVecR * p.ld;
+    }
+    // forward SDE: offset c_k = a_k - x0 of the anchor of the level-k regression
+    __device__ __forceinline__ Real *anchor(int s, int k) const
+    {
+        return reinterpret_cast<Real *>(p.anchor) + ((size_t)s * (p.N + 1) + k) * p.ld;
     }
 };
 
@@ -603,7 +632,7 @@ __global__ void __launch_bounds__(256) k_update(Params p)
             const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) dl[v] = ld_chunk(drow + c * E);
         }
-        Real acc[kSegSums] = {Real(0), Real(0), Real(0), Real(0)};
+        Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int c = seg * 32 * VPT + lane + 32 * v;
@@ -659,23 +688,56 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
     SolveState &st = p.st[s];
     const bool terminal = p.level == p.N;
     const double t_k = p.level * p.dt;
-    const double rho_ref = p.sigma * p.sigma * p.d * t_k;
+    // kernel scale: E|Delta_k|^2 = sigma^2 d t_k without a drift; the cloud's mean squared
+    // distance to the anchor (k_sde_rho) with one
+    const double rho_ref = p.sde ? st.rho_ref : p.sigma * p.sigma * p.d * t_k;
     const double yref = terminal ? st.gx0 : st.alpha;
     double sums[3] = {0.0, 0.0, 0.0};
     int it_used = 0, failed = 0;
     if (j < p.M) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0;
         for (int seg = 0; seg < p.nseg; ++seg) {
             const Real *sp = ws.segp(s, j, seg);
             a0 += (double)sp[0];
             a1 += (double)sp[1];
             a2 += (double)sp[2];
             a3 += (double)sp[3];
+            if (p.sde) {
+                a4 += (double)sp[4];
+                a5 += (double)sp[5];
+            }
         }
         double Yj, rho, dot = 0.0;
-        if (terminal) {
+        if (p.sde) {
+            // rows of k_sde_rows: [0] alpha_x . Delta, [1] |Delta|^2, [2] |Delta - c_{k-1}|^2,
+            // [3] g . Delta, [4], [5] feature sums.  Level k < N: the prediction at the drifted
+            // position, alpha + alpha_x . (Delta + mu(x0 + Delta) dt) with alpha the intercept
+            // at Delta = 0, and Z = sigma(X)^T alpha_x, so sum_i z_i = sigma sum alpha_x +
+            // sig1 alpha_x . (x0 + Delta) and |z|^2 = sigma^2 |alpha_x|^2 (sig1 = 0 there).
+            if (terminal) {
+                Yj = g_value(p, a4);
+            } else {
+                const double E_hat = st.alpha + (1.0 + p.mu1 * p.dt) * a0 +
+                                     p.dt * (p.mu0 * st.sum_ax + p.mu1 * st.ax_x0);
+                const double sumz = st.sumz + p.sig1 * (st.ax_x0 + a0);
+                const double feat = p.kind == FBSDE_AC_MANUFACTURED
+                                        ? f_feature(p, t_k, a4, 0.0, 0.0)
+                                        : f_feature(p, t_k, a4, sumz, st.zz, a5);
+                int it;
+                Yj = newton(p, E_hat, feat, it);
+                if (it < 0) {
+                    failed = 1;
+                    it_used = p.newton_max_iter;
+                } else {
+                    it_used = it;
+                }
+            }
+            rho = a2;   // distance to the anchor: the kernel weight
+            a2 = a1;    // |Delta|^2: the trace of the weighted covariance (shift-free)
+        } else if (terminal) {
             rho = a0;
             Yj = g_value(p, a1);
+            a2 = rho;
         } else {
             dot = a0;
             rho = a1;
@@ -690,6 +752,7 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
             } else {
                 it_used = it;
             }
+            a2 = rho;
         }
         const Real wr = (Real)kernel_weight(p, rho, rho_ref);
         const double wd = (double)wr;
@@ -705,7 +768,7 @@ __global__ void __launch_bounds__(256) k_particles(Params p)
         cf[2] = (Real)(wd * a3);   // D . (starting guess of the next level's solve)
         sums[0] = wd;
         sums[1] = wd * (Yj - yref);
-        sums[2] = wd * rho;
+        sums[2] = wd * a2;
     }
     block_sum(sums, sm);
     if (threadIdx.x == 0) {
@@ -1021,7 +1084,8 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
     const WS<Real> ws(p);
     double *x = ws.v64(s, 0), *x0v = ws.v64(s, 6);
     Real *pR = ws.vR(s, 0), *xR = ws.vR(s, 1), *x0R = ws.vR(s, 2);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // sum cos, sum x, sum x^2, theta-weighted sum
+    // sum cos, sum x, sum x^2, theta-weighted sum, the two drift kinds' psi at x0
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = i < p.d ? x0[(size_t)s * p.d + i] : 0.0;
@@ -1040,6 +1104,11 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
             acc[1] += xi;
             acc[2] += xi * xi;
             acc[3] += p.kind == FBSDE_HJB_LOGQUAD ? th * xi * xi : th * xi;
+            if (p.sde) {
+                const double sg = p.sigma + p.sig1 * xi, m = p.mu0 + p.mu1 * xi;
+                acc[4] += 0.5 * sg * sg * cos(xi) + m * sin(xi);
+                acc[5] += sg * sg + 2.0 * m * xi;
+            }
         }
     }
     block_sum(acc, sm);
@@ -1053,8 +1122,12 @@ __global__ void __launch_bounds__(kFinThreads) k_setup(Params p, const double *x
         case FBSDE_HJB_LOGQUAD:
         case FBSDE_AFFINE_TEST: phi = acc[3]; break;
         case FBSDE_AC_DOUBLEWELL: phi = acc[2]; break;
+        case FBSDE_DRIFT_AC: phi = acc[0]; st.psi0 = acc[4]; break;
+        case FBSDE_DRIFT_QUAD: phi = acc[2]; st.psi0 = acc[5]; break;
         }
-        st.phi0 = acc[0];
+        // phi0: the feature sum of f at x0 (sum cos x0 of the Allen-Cahn source; phi of g for
+        // the drift kinds)
+        st.phi0 = p.kind == FBSDE_DRIFT_QUAD ? acc[2] : acc[0];
         st.gx0 = g_value(p, phi);
         st.yref = st.gx0;
         p.st[s] = st;
@@ -1272,7 +1345,10 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
     const double *S = ws.v64(s, 3);
     Real *xR = ws.vR(s, 1), *gR = ws.vR(s, 3);
     const bool extrap = k + 1 < p.N;   // alpha_x of level k+1 is in slot 8
-    double a[3] = {0.0, 0.0, 0.0};
+    // S . alpha_x, sum alpha_x, |alpha_x|^2; forward SDE: alpha_x . x0, alpha_x . c_k
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const double *x0v = ws.v64(s, 6);
+    const Real *ck = p.sde ? ws.anchor(s, k) : nullptr;
     #pragma unroll 4
     for (int i = threadIdx.x; i < p.ld; i += blockDim.x) {
         const double xi = x[i];
@@ -1284,6 +1360,10 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
         a[0] += S[i] * xi;
         a[1] += xi;
         a[2] += xi * xi;
+        if (ck) {
+            a[3] += xi * x0v[i];
+            a[4] += xi * (double)ck[i];
+        }
         if (i < p.d) {
             if (p.tr_alpha_x) p.tr_alpha_x[((size_t)s * p.N + k) * p.d + i] = xi;
             if (k == 0 && p.grad) p.grad[(size_t)s * p.d + i] = xi;
@@ -1297,14 +1377,25 @@ __global__ void __launch_bounds__(kFinThreads) k_cg_post(Params p)
         st.yref = alpha;
         st.sumz = p.sigma * a[1];
         st.zz = p.sigma * p.sigma * a[2];
+        st.sum_ax = a[1];
+        st.ax_x0 = a[3];
         st.newton_max = 0;
-        if (p.tr_alpha) p.tr_alpha[(size_t)s * p.N + k] = alpha;
+        // the traced intercept is the model's value at the anchor (D = 0): with a drift the
+        // rows are centred at x0, so the intercept there moves by alpha_x . c_k
+        if (p.tr_alpha) p.tr_alpha[(size_t)s * p.N + k] = alpha + a[4];
         if (p.tape_s) p.tape_s[((size_t)s * p.N + k) * 4 + 2] = alpha;
         if (p.tr_cg) p.tr_cg[(size_t)s * p.N + k] = st.iters;
         if (k == 0) {
-            const double feat = f_feature(p, 0.0, st.phi0, st.sumz, st.zz);
+            // every particle of level 0 sits at x0 (Delta_0 = 0): one Newton solve; with a
+            // drift the prediction is taken at x0 + mu(x0) dt and sum_i z_i at sigma(x0)
+            double E_hat = alpha, sumz = st.sumz;
+            if (p.sde) {
+                E_hat += p.dt * (p.mu0 * a[1] + p.mu1 * a[3]);
+                sumz += p.sig1 * a[3];
+            }
+            const double feat = f_feature(p, 0.0, st.phi0, sumz, st.zz, st.psi0);
             int it;
-            const double u = newton(p, alpha, feat, it);
+            const double u = newton(p, E_hat, feat, it);
             if (it < 0 && st.status == 0) st.status = FBSDE_ERR_NEWTON;
             const int used = it < 0 ? p.newton_max_iter : it;
             st.newton_max_all = max(st.newton_max_all, used);

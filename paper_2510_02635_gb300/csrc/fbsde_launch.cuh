@@ -3,6 +3,7 @@
 #include "fbsde_adjoint.cuh"
 #include "fbsde_kernels.cuh"
 #include "fbsde_matvec.cuh"
+#include "fbsde_sde.cuh"
 #include "fbsde_step.cuh"
 
 namespace fbsde {
@@ -54,6 +55,50 @@ cudaError_t Launch<Real>::update(const Params &p, const Layout &L, cudaStream_t 
     q.wa = p.walk < 0 ? a : 1.0 / a;
     q.wb = p.walk < 0 ? b : -b / a;
     FBSDE_SEG_DISPATCH(k_update, q)
+}
+
+// Forward SDE with a drift or a state-dependent diffusion (fbsde_sde.cuh).
+template <typename Real>
+cudaError_t Launch<Real>::sde_anchor(const Params &p, const Layout &L, cudaStream_t s)
+{
+    const long long n = (long long)L.Q * L.ld;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    dev::k_sde_anchor<Real><<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Euler-Maruyama step k -> k + 1 (0 <= k < N) from the rows `from` (nullptr: Delta_0 = 0)
+// into `to` (may equal `from`), each [Q][M][ld].
+template <typename Real>
+cudaError_t Launch<Real>::sde_forward(const Params &p, const Layout &L, int k, const void *from,
+                                      void *to, cudaStream_t s)
+{
+    if (k < 0 || k >= p.N || !to) return cudaErrorInvalidValue;
+    const long long n = (long long)L.Q * L.M * (L.ld * (long long)L.real_sz / 16);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    dev::k_sde_forward<Real><<<blocks, 256, 0, s>>>(p, k, static_cast<const Real *>(from),
+                                                   static_cast<Real *>(to));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::sde_rows(const Params &p, const Layout &L, int k, cudaStream_t s)
+{
+    if (k < 1 || k > p.N) return cudaErrorInvalidValue;
+    switch (L.seg_vpt) {
+    case 1: dev::k_sde_rows<Real, 1><<<L.row_blocks, 256, 0, s>>>(p, k); break;
+    case 2: dev::k_sde_rows<Real, 2><<<L.row_blocks, 256, 0, s>>>(p, k); break;
+    case 4: dev::k_sde_rows<Real, 4><<<L.row_blocks, 256, 0, s>>>(p, k); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t Launch<Real>::sde_rho(const Params &p, const Layout &L, cudaStream_t s)
+{
+    dev::k_sde_rho<Real><<<L.Q, kFinThreads, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <typename Real>

@@ -30,6 +30,8 @@ KINDS = {
     "cubic_test": 4,
     "ac_doublewell": 5,
     "cos_linear_test": 6,
+    "drift_ac": 7,
+    "drift_quad": 8,
 }
 PRECISIONS = {"fp32": FBSDE_FP32, "fp64": FBSDE_FP64}
 
@@ -42,6 +44,7 @@ class fbsde_problem(C.Structure):
         ("c3", C.c_double), ("h", C.c_double), ("ridge_rel", C.c_double),
         ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("newton_max_iter", C.c_int32),
         ("newton_tol", C.c_double), ("ctas", C.c_int32), ("reserved", C.c_int32),
+        ("mu0", C.c_double), ("mu1", C.c_double), ("sig1", C.c_double),
     ]
 
 
@@ -172,14 +175,16 @@ def make_problem(kind: str, d: int, N: int, M: int, sigma: float, T: float,
                  c1: float = 0.0, c2: float = 0.0, c3: float = 0.0, h: float = 2.0,
                  ridge_rel: float = 1e-3, cg_tol: float = 1e-6, cg_max_iter: int = 0,
                  newton_max_iter: int = 0, newton_tol: float = 0.0,
-                 ctas: int = 0) -> fbsde_problem:
+                 ctas: int = 0, mu0: float = 0.0, mu1: float = 0.0,
+                 sig1: float = 0.0) -> fbsde_problem:
     """Fill the C problem struct; theta is a device tensor (or host array for the
-    host-buffer entry point) whose storage must outlive the call."""
+    host-buffer entry point) whose storage must outlive the call.  mu0, mu1, sig1: the
+    forward SDE's drift mu0 + mu1 x_i and diffusion sigma + sig1 x_i (zero: driftless)."""
     return fbsde_problem(KINDS[kind], int(d), int(N), PRECISIONS[precision], int(M),
                          float(sigma), float(T), _ptr(theta), float(A), float(c0), float(c1),
                          float(c2), float(c3), float(h), float(ridge_rel), float(cg_tol),
                          int(cg_max_iter), int(newton_max_iter), float(newton_tol), int(ctas),
-                         0)
+                         0, float(mu0), float(mu1), float(sig1))
 
 
 def fbsde_workspace_bytes(problem: fbsde_problem, Q: int) -> int:

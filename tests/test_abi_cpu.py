@@ -47,7 +47,7 @@ def test_binding_constants_match_the_header():
 
 
 def test_abi_version_and_status_strings(lib):
-    assert fbsde.fbsde_abi_version() == 1
+    assert fbsde.fbsde_abi_version() == 2
     assert fbsde.fbsde_status_string(0) == "ok"
     assert "argument" in fbsde.fbsde_status_string(1)
     assert fbsde.fbsde_status_string(99) == "unknown status"
@@ -195,3 +195,38 @@ def test_batch_argument_errors_return_synchronously(lib):
     assert lib.fbsde_solve_batch(C.byref(p), 64, 1, None, 0, 0, fake, None, fake, n, None) == 1
     assert lib.fbsde_solve_batch(C.byref(p), 64, 1, fake, 0, 0, fake, None, fake, n - 1, None) == 2
     assert lib.fbsde_solve_batch(None, 64, 1, fake, 0, 0, fake, None, fake, n, None) == 1
+
+
+def test_forward_sde_workspace_and_argument_checks(lib):
+    """A drift, a state-dependent diffusion or a drift kind adds the stored levels of the
+    Euler-Maruyama rows (checkpoints every s = ceil(sqrt N) levels below N plus one segment
+    of s - 1 levels) and the anchor offsets [Q][N+1][ld]; the driftless problem is
+    unchanged.  HJB_LOGQUAD needs sig1 = 0, the coefficients must be finite, and the
+    adjoint and per-anchor entry points take only the driftless scheme."""
+    Q, d, M, N = 2, 100, 2048, 10
+    base = fbsde.fbsde_workspace_bytes(_prob(d=d, M=M, N=N), Q)
+    s = math.ceil(math.sqrt(N))
+    slots = (N - 1) // s + s - 1
+    slab = Q * M * d * 4
+    for kw in (dict(mu0=0.1), dict(mu1=-0.5), dict(sig1=0.2), dict(kind="drift_ac"),
+               dict(kind="drift_quad")):
+        n = fbsde.fbsde_workspace_bytes(_prob(d=d, M=M, N=N, **kw), Q)
+        # (the driftless FP32 problem sizes its partials for the fused step; the drift
+        # path does not use it, so the rest of the layout differs by a little)
+        assert slots * slab < n - base <= slots * slab + 2 * Q * (N + 1) * d * 4 + 4096
+    # FP64 (no fused step either way): exactly the stored slabs plus the anchor offsets
+    up = lambda x: (x + 255) // 256 * 256
+    for N1, slots1 in ((1, 0), (2, 1), (4, 2), (9, 4), (10, 5), (17, 7)):
+        n0 = fbsde.fbsde_workspace_bytes(_prob(d=d, M=M, N=N1, precision="fp64"), Q)
+        n1 = fbsde.fbsde_workspace_bytes(_prob(d=d, M=M, N=N1, precision="fp64", mu1=-1.0), Q)
+        assert n1 - n0 == up(slots1 * Q * M * d * 8) + up(Q * (N1 + 1) * d * 8), N1
+    assert fbsde.fbsde_workspace_bytes(_prob(kind="hjb_logquad", sig1=0.1), 1) == 0
+    assert fbsde.fbsde_workspace_bytes(_prob(kind="hjb_logquad", mu0=0.1), 1) > 0
+    for bad in (dict(mu0=math.nan), dict(mu1=math.inf), dict(sig1=-math.inf)):
+        assert fbsde.fbsde_workspace_bytes(_prob(**bad), 1) == 0
+    assert fbsde.fbsde_anchored_workspace_bytes(_prob(mu1=-0.3)) == 0
+    assert fbsde.fbsde_anchored_workspace_bytes(_prob(kind="drift_ac")) == 0
+    fake = C.c_void_p(1 << 20)
+    p = _prob(mu0=0.2)
+    assert lib.fbsde_adjoint(C.byref(p), 1, fake, 0, 0, fake, fake, None, fake, None, fake,
+                             1 << 40, None) == 1
