@@ -249,8 +249,10 @@ FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const doub
  * to the batch (weights normalised over it); K = M is fbsde_solve_anchored.
  *   2 <= K <= M, else FBSDE_ERR_ARG; every other argument, the workspace
  *   (fbsde_anchored_workspace_bytes), the blocking behaviour and the return codes are those
- *   of fbsde_solve_anchored.  The contractions still run over all M particles (cost
- *   O(M^2 d) per level and pass); the weights outside the window are zero.
+ *   of fbsde_solve_anchored.  The weights outside the window are zero, and the products
+ *   skip the tiles and K-splits that lie wholly outside the band of the windows, so a CG
+ *   pass costs O(M (K + 128) d) in its contractions; the results equal those of the
+ *   products over all M particles.
  */
 FBSDE_API int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
                                 uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,

@@ -382,7 +382,8 @@ def solve_neighbours(prob: Problem, K: int, x0, seed: int, solve_index: int = 0)
 def solve_batch(prob: Problem, K: int, x0, seed: int, solve_index: int = 0) -> dict:
     """Algorithm 1 with one regression per particle anchor over a batch of K particles, the
     cyclic window j = (m + q) mod M of anchor m (the random-batch reading of Remark 2.1; the
-    paths are i.i.d., so the window is a random batch in law).  K = M is solve_anchored."""
+    paths are i.i.d., so the window holds the anchor's own path and a random sample of K - 1
+    others).  K = M is solve_anchored."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     assert x0.shape == (prob.d,)
     u0 = C.c_double(math.nan)

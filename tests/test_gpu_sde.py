@@ -43,6 +43,7 @@ CASES = [
     ("ac_manufactured", 50, 333, 3, 1.0, 0.5, (0.3, 0.0, 0.2), {}),
     ("ac_doublewell", 20, 290, 2, math.sqrt(2.0), 0.3, (0.1, -0.3, 0.1), {}),
     ("cos_linear_test", 29, 211, 1, 1.0, 0.4, (0.1, 0.2, 0.1), {"c1": 0.4}),
+    ("cubic_test", 24, 230, 3, 1.0, 0.3, (0.1, -0.2, 0.1), {"A": 0.5}),
     ("drift_quad", 12, 500, 17, 0.6, 0.5, (-0.2, -1.0, 0.3), {}),
 ]
 
