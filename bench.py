@@ -490,6 +490,48 @@ def extra_logistic() -> dict:
             "ms_per_step": ms}
 
 
+def extra_drift() -> dict:
+    """Row f4: the forward SDE with an Ornstein-Uhlenbeck drift and a state-dependent
+    diffusion (Euler-Maruyama paths kept at checkpoints, segments recomputed), d = 1000,
+    16 queries, FP32: time per solve, the per-family split of one more solve, the
+    Euler-Maruyama kernel's algorithmic bandwidth (8 B per particle-dim per step; the
+    first step of a sweep only writes) and the error against the closed form."""
+    import numpy as np
+    import torch
+
+    from paper_2510_02635_gb300 import fbsde
+    w = W.F4_DRIFT_AC_D1000
+    inp = W.inputs(w)
+    x0 = torch.tensor(inp["x0"], device="cuda")
+    solver = fbsde.Solver(w.kind, w.d, w.N, w.M, w.sigma, w.T, Q=w.Q, precision=w.precision,
+                          h=w.h, ridge_rel=w.ridge_rel, cg_tol=w.cg_tol, **w.extra)
+    ms = _events_ms(lambda: solver.solve(x0, seed=w.seed, check_status=False), 3)
+    out = solver.solve(x0, seed=w.seed)
+    torch.cuda.synchronize()
+    rec = {"workload": w.name, "ms_per_solve": ms, "status": out["status"],
+           "value": w.particle_dim_updates / (ms * 1e-3), "unit": UNIT}
+    fbsde.fbsde_profile_start(1 << 16)
+    solver.solve(x0, seed=w.seed, check_status=False)
+    torch.cuda.synchronize()
+    split = fbsde.fbsde_profile_stop()
+    rec["kernels_ms_per_solve"] = {k: v["total_ms"] for k, v in split.items() if v["launches"]}
+    em = split["forward"]
+    pdims = w.Q * w.M * w.d
+    em_bytes = (8 * em["launches"] - 4) * pdims
+    if em["total_ms"] > 0:
+        rec["euler_maruyama"] = {"launches_per_solve": em["launches"],
+                                 "gbs": em_bytes / (em["total_ms"] * 1e-3) / 1e9,
+                                 "note": "N forward steps + the levels recomputed from "
+                                         "checkpoints on the way back; timed one by one "
+                                         "with the launch profiler"}
+    if out["status"] == 0:
+        u = out["u0"].cpu().numpy()
+        errs = [abs(float(u[q]) - W.exact_solution(w, inp["x0"][q])[0]) /
+                abs(W.exact_solution(w, inp["x0"][q])[0]) for q in range(w.Q)]
+        rec["rel_err_u_closed_form"] = {"max": max(errs), "mean": float(np.mean(errs))}
+    return rec
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank: int, world: int) -> None:
     import numpy as np
@@ -632,7 +674,8 @@ def run_gpu(args, rank: int, world: int) -> None:
         del ws
         torch.cuda.empty_cache()
         extras = {"batched": extra_batched(), "adjoint": extra_adjoint(),
-                  "logistic_d1000_plan": extra_logistic(), "per_anchor": extra_anchored()}
+                  "logistic_d1000_plan": extra_logistic(), "per_anchor": extra_anchored(),
+                  "drift": extra_drift()}
 
     if single is not None:
         cpu["single_thread"] = finish_single_thread_baseline(single)

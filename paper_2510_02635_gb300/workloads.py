@@ -77,15 +77,20 @@ def exact_solution(w: Workload, x0) -> tuple[float, np.ndarray] | None:
     kinds without one.  These are properties of the test problems (checked against the PDE
     (2.1) symbolically by the oracle tests), not arithmetic of the scheme:
       Allen-Cahn with manufactured source: u = e^{t - T} (1/d) sum_i cos x_i;
-      gradient-dependent logistic driver (sigma = d): u = 1 / (1 + exp(-(t + sum_i x_i / d))).
+      gradient-dependent logistic driver (sigma = d): u = 1 / (1 + exp(-(t + sum_i x_i / d)));
+      drift kinds (any affine drift and diffusion): u = e^{t - T} (1/d) sum_i cos x_i, or
+      e^{t - T} (1/d) sum_i x_i^2.
     """
     x0 = np.asarray(x0, dtype=np.float64)
-    if w.kind == "ac_manufactured":
+    if w.kind in ("ac_manufactured", "drift_ac"):
         e = math.exp(-w.T)
         return e * float(np.mean(np.cos(x0))), -e * np.sin(x0) / w.d
     if w.kind == "logistic_grad" and w.sigma == float(w.d):
         u = 1.0 / (1.0 + math.exp(-float(np.sum(x0)) / w.d))
         return u, np.full(w.d, u * (1.0 - u) / w.d)
+    if w.kind == "drift_quad":
+        e = math.exp(-w.T)
+        return e * float(np.mean(x0 * x0)), 2.0 * e * x0 / w.d
     return None
 
 
@@ -104,6 +109,11 @@ C2_AC_D10000 = Workload("ac_manufactured_d10000_M16384_N50_Q16", "ac_manufacture
 C4_HJB_D1000 = Workload("hjb_logquad_d1000_M4096_N20_Q1", "hjb_logquad", d=1000,
                         sigma=math.sqrt(2.0), T=1.0, N=20, M=4096, Q=1, seed=4,
                         x0_law="normal_1/d", theta_law="uniform_0.5_1.5")
+# Forward SDE with an Ornstein-Uhlenbeck drift and a state-dependent diffusion (drift
+# mu_i = 0.1 - 0.8 x_i, diffusion 0.5 + 0.2 x_i), manufactured Allen-Cahn-type source.
+F4_DRIFT_AC_D1000 = Workload("drift_ac_ou_d1000_M4096_N20_Q16", "drift_ac", d=1000, sigma=0.5,
+                             T=0.6, N=20, M=4096, Q=16, seed=6, x0_law="normal_1/d",
+                             extra={"mu0": 0.1, "mu1": -0.8, "sig1": 0.2})
 # Sec. 4.1, case 1 of the paper: double-well Allen-Cahn, d = 100, T = 0.3, x0 = 0,
 # generator Lap u (sigma = sqrt 2); printed reference u(0,0) ~ 0.0528.
 AC_CASE1_D100 = Workload("ac_doublewell_d100_T0.3", "ac_doublewell", d=100,
