@@ -316,11 +316,18 @@ def extra_batched(sample: int = 32) -> dict:
     create_s = time.perf_counter() - t0
     ms_full = _events_ms(batch.launch, 2)
     status = int(batch.plan.diagnostics().status)
-    # algorithmic bytes of one batch: per instance 4 B per particle-dim for the forward
-    # write, 12 B per particle-dim per level (update read + write, moments read) and 4 B
-    # per particle-dim per CG product
+    # algorithmic bytes of one batch, per instance in units of one pass over its rows
+    # (4 B per particle-dim in FP32, 8 B in FP64): the fused step (FP32, d <= 10240) writes
+    # the end point once and reads + writes the rows at each of the N - 1 levels; the
+    # unfused path writes the end point, reads it for the first moments, and reads +
+    # writes + reads again at each level; every CG product reads the rows once
     cg = [int(batch.plan.instance_diagnostics(i).cg_iters_total) for i in range(len(inst))]
-    nbytes = sum(4.0 * w.M * w.d * (1 + 3 * w.N + c) for w, c in zip(inst, cg))
+
+    def passes(w, c):
+        fused = w.precision == "fp32" and (w.d + 3) // 4 * 4 <= 10240
+        return (1 + 2 * (w.N - 1) if fused else 2 + 3 * (w.N - 1)) + c
+    nbytes = sum((4.0 if w.precision == "fp32" else 8.0) * w.M * w.d * passes(w, c)
+                 for w, c in zip(inst, cg))
     batch.close()
     units_full = sum(w.M * w.d * w.N for w in inst)
     sub, subx = inst[:sample], x0s[:sample]

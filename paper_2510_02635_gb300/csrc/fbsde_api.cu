@@ -97,8 +97,18 @@ int make_layout(const fbsde_problem *P, int32_t Q, Layout &L)
         const size_t stage_target = 32 * 1024, ring_target = 200 * 1024;
         long long R = std::max<long long>(1, (long long)(stage_target / row_bytes));
         R = std::max<long long>(L.teams, R / L.teams * L.teams);
+        long long S = std::min<long long>(8, std::max<long long>(2, ring_target / (R * row_bytes)));
+        // a CTA never needs a ring larger than its own rows: small instances keep their
+        // ring, and so their shared memory, small (two stages of at most half their rows),
+        // which lets the CTAs of concurrent instances share an SM
+        const long long rows_cta = (P->M + L.G - 1) / L.G;
+        if (S * R > rows_cta) {
+            const long long half = ((rows_cta + 1) / 2 + L.teams - 1) / L.teams * L.teams;
+            R = std::min<long long>(R, std::max<long long>(L.teams, half));
+            S = std::max<long long>(2, std::min<long long>(S, (rows_cta + R - 1) / R));
+        }
         L.mv_rows = (int)R;
-        L.mv_stages = (int)std::min<long long>(8, std::max<long long>(2, ring_target / (R * row_bytes)));
+        L.mv_stages = (int)S;
         L.mv_smem = (size_t)L.mv_stages * R * row_bytes + 2 * L.mv_stages * sizeof(uint64_t) +
                     (size_t)L.teams * 2 * 32 * L.real_sz;
         if (L.mv_smem > 227 * 1024) return FBSDE_ERR_ARG;
@@ -915,6 +925,12 @@ size_t fbsde_plan_workspace_bytes(int32_t n, const fbsde_instance *inst)
     return plan_layout(n, inst, v, total) == FBSDE_OK ? total : 0;
 }
 
+// Scheduling model of a CG pass for the plan's branches: the launches of a pass (product,
+// reduction, update) cost about 25 us however small the instance, and its rows stream at
+// about 6.5 TB/s.
+constexpr double kPassLatency = 25e-6;
+constexpr double kPassBandwidth = 6.5e12;
+
 int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, int32_t branches,
                       void *workspace, size_t workspace_bytes)
 {
@@ -949,17 +965,21 @@ int fbsde_plan_create(fbsde_plan **plan, int32_t n, const fbsde_instance *inst, 
     // largest-first list scheduling of the instances over the branches
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    // work estimate: Q M d N times the passes per level, 2 + the CG iterations, which
-    // grow like the square root of the condition number of the regression: for a cloud
-    // of M points in d dimensions (ratio rho = min(d/M, M/d)) the extreme eigenvalues
-    // are near (1 -+ sqrt(rho))^2, and the ridge bounds the smallest from below.
+    // time estimate: N levels times the passes per level, 2 + the CG iterations, which
+    // grow like the square root of the condition number of the regression (for a cloud
+    // of M points in d dimensions, ratio rho = min(d/M, M/d), the extreme eigenvalues
+    // are near (1 -+ sqrt(rho))^2, and the ridge bounds the smallest from below), times
+    // the time of a pass: a fixed latency of its launches plus its rows at the HBM
+    // bandwidth.  Without the latency term the many small instances look free and pile
+    // up on a few branches as long chains of latency-bound passes.
     auto cost = [&](int i) {
         const fbsde_problem &P = v[i].in.problem;
         const double rho = std::min((double)P.d / P.M, (double)P.M / P.d);
         const double hi = (1.0 + std::sqrt(rho)) * (1.0 + std::sqrt(rho));
         const double lo = std::max((1.0 - std::sqrt(rho)) * (1.0 - std::sqrt(rho)),
                                    std::max(P.ridge_rel, 1e-6) * hi);
-        return (double)v[i].in.Q * P.M * P.d * P.N * (2.0 + std::sqrt(hi / lo));
+        const double bytes = (double)v[i].in.Q * P.M * P.d * (P.precision == FBSDE_FP32 ? 4 : 8);
+        return (double)P.N * (2.0 + std::sqrt(hi / lo)) * (kPassLatency + bytes / kPassBandwidth);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::vector<double> load(B, 0.0);
