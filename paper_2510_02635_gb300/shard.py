@@ -53,13 +53,14 @@ def gather_queries(local: np.ndarray, q_total: int, device="cpu") -> np.ndarray:
 
 
 def instance_cost(w) -> float:
-    """Estimated work of one instance: Q M d N particle-dims per pass times the passes per
-    level, 2 + sqrt(kappa) (the row step and the moments, then CG passes growing like the
-    square root of the regression's condition number kappa, estimated from the
-    Marchenko-Pastur edges of the cloud's covariance and the ridge).  The plan's branch
-    scheduler uses a model of the same form."""
+    """Estimated time of one instance, in seconds: N levels of 2 + sqrt(kappa) passes over
+    its rows (the row step and the moments, then CG passes growing like the square root of
+    the regression's condition number kappa, estimated from the Marchenko-Pastur edges of
+    the cloud's covariance and the ridge), each pass a fixed launch latency of 25 us plus
+    its rows at 6.5 TB/s.  The plan's branch scheduler uses the same model."""
     from .autotune import kappa_estimate
-    return float(w.Q) * w.M * w.d * w.N * (2.0 + math.sqrt(kappa_estimate(w)))
+    nbytes = float(w.Q) * w.M * w.d * (4.0 if w.precision == "fp32" else 8.0)
+    return w.N * (2.0 + math.sqrt(kappa_estimate(w))) * (25e-6 + nbytes / 6.5e12)
 
 
 def cost_shard(instances, world: int) -> list[list[int]]:
