@@ -438,9 +438,12 @@ def extra_anchored() -> dict:
     status = [0]
 
     def run():
-        status[0] = fbsde.fbsde_solve_anchored(p, 1, x0, w.seed, 0, u, g, ws)
+        fbsde.check(fbsde.fbsde_solve_anchored(p, 1, x0, w.seed, 0, u, g, ws))
 
     ms = _events_ms(run, 3)
+    dg = fbsde.fbsde_anchored_diagnostics(p, ws)
+    status[0] = int(dg.status)
+    passes_full = dg.cg_iters_total / w.N
     u_anchored = float(u[0])
     single = fbsde.Solver(w.kind, w.d, w.N, w.M, w.sigma, w.T, Q=1, precision=w.precision,
                           h=w.h, ridge_rel=w.ridge_rel, cg_tol=w.cg_tol)
@@ -449,7 +452,7 @@ def extra_anchored() -> dict:
     out = {"workload": "ac_manufactured_d100_M2048_N10_Q1_fp32_per_anchor", "ms_per_solve": ms,
            "status": status[0], "unit_note": "M^2 d N anchor-particle-dims per solve",
            "u0_single_anchor": u_single, "u0_exact": exact,
-           "abs_err_single_anchor": abs(u_single - exact)}
+           "abs_err_single_anchor": abs(u_single - exact), "cg_passes_per_level": passes_full}
     if status[0] == 0:   # a failed solve reports its status only
         out.update(value=w.M * w.M * w.d * w.N / (ms * 1e-3), u0=u_anchored,
                    abs_err=abs(u_anchored - exact))
@@ -467,11 +470,14 @@ def extra_anchored() -> dict:
             st_b = [0]
 
             def run_batch():
-                st_b[0] = fbsde.fbsde_solve_batch(pb, K, 1, x0, w.seed, 0, u, g, wsb)
+                fbsde.check(fbsde.fbsde_solve_batch(pb, K, 1, x0, w.seed, 0, u, g, wsb))
 
             ms_b = _events_ms(run_batch, 3)
+            dgb = fbsde.fbsde_anchored_diagnostics(pb, wsb)
+            st_b[0] = int(dgb.status)
             u_b = float(u[0])
-            rec = {"K": K, "M": Mb, "ms_per_solve": ms_b, "status": st_b[0]}
+            rec = {"K": K, "M": Mb, "ms_per_solve": ms_b, "status": st_b[0],
+                   "cg_passes_per_level": dgb.cg_iters_total / w.N}
             if st_b[0] == 0:
                 rec.update(u0=u_b, abs_err=abs(u_b - exact))
             out["batch"].append(rec)

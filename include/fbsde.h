@@ -229,15 +229,27 @@ FBSDE_API int fbsde_solve_noalloc(const fbsde_problem *P, int32_t Q, const doubl
  *   Same arguments as fbsde_solve (no trace); M <= 32768; theta (if the kind needs it)
  *   is a device pointer in P->theta; workspace >= fbsde_anchored_workspace_bytes(P)
  *   bytes, 256-byte aligned, reused for the Q queries one after the other.
- * The call blocks the host: it reads the count of anchors still iterating every four CG
- * passes.  Returns FBSDE_OK, an argument error, or the first device status (FBSDE_ERR_CG,
+ * Asynchronous on the stream like fbsde_solve: the call is captured once into a CUDA graph
+ * (each level's CG passes a conditional while node that repeats while some anchor iterates
+ * on), cached per device and argument list, and launched; a stream that is itself being
+ * captured receives the work directly.  Returns FBSDE_OK, an argument error
+ * (FBSDE_ERR_ARG, FBSDE_ERR_WORKSPACE) or FBSDE_ERR_CUDA; the device status (FBSDE_ERR_CG,
  * FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE, or FBSDE_ERR_TIMEOUT when a tensor-core pipeline
- * wait ran out).
+ * wait ran out) is read after the work with fbsde_anchored_diagnostics.
  */
 FBSDE_API size_t fbsde_anchored_workspace_bytes(const fbsde_problem *P);
 FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, uint64_t seed,
                                    uint32_t solve_index0, double *u0, double *grad_u0,
                                    void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
+/* Status of the last fbsde_solve_anchored / fbsde_solve_batch call on this workspace:
+ * copies its status word on `stream` and waits for the stream (host-synchronising).
+ * out->status: the first device status of any query; out->cg_iters_total: CG passes over
+ * all levels and queries (each pass serves every anchor still iterating); the other fields
+ * are 0.  Returns FBSDE_ERR_ARG for an invalid P or a NULL pointer, FBSDE_ERR_CUDA if the
+ * copy fails. */
+FBSDE_API int fbsde_anchored_diagnostics(const fbsde_problem *P, const void *workspace,
+                                         fbsde_diag *out, fbsde_stream_t stream);
 
 /* Algorithm 1 per particle anchor, each anchor's regression over a batch of K particles
  * (the batch reading of Remark 2.1): for anchor m the batch is the cyclic window
@@ -248,8 +260,8 @@ FBSDE_API int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const doub
  * Gaussian weights, the moments and the ridge are those of fbsde_solve_anchored restricted
  * to the batch (weights normalised over it); K = M is fbsde_solve_anchored.
  *   2 <= K <= M, else FBSDE_ERR_ARG; every other argument, the workspace
- *   (fbsde_anchored_workspace_bytes), the blocking behaviour and the return codes are those
- *   of fbsde_solve_anchored.  The weights outside the window are zero, and the products
+ *   (fbsde_anchored_workspace_bytes), the asynchronous launch and the return codes are
+ *   those of fbsde_solve_anchored (status through fbsde_anchored_diagnostics).  The weights outside the window are zero, and the products
  *   skip the tiles and K-splits that lie wholly outside the band of the windows, so a CG
  *   pass costs O(M (K + 128) d) in its contractions; the results equal those of the
  *   products over all M particles.

@@ -26,6 +26,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <list>
+#include <mutex>
 #include <vector>
 
 #include "fbsde_kernels.cuh"
@@ -502,7 +504,6 @@ namespace {
 constexpr size_t kAl = 256;
 inline size_t up(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 constexpr int64_t kMaxM = 32768;   // three M x M matrices per call
-constexpr int kCheckEvery = 4;     // CG passes between host checks of the active count
 
 struct Lay {
     int d, ld, N;
@@ -560,7 +561,7 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.an = take(M * 8);
     L.cs = take((size_t)L.nrc * M * 3 * 8);
     L.st = take(M * sizeof(Anchor));
-    L.cnt = take(2 * sizeof(int));
+    L.cnt = take(4 * sizeof(int));
     L.total = o;
     return true;
 }
@@ -689,13 +690,37 @@ cudaError_t gemm(int Mr, int Nc, int K, int kc, const Real *A, int lda, const Re
         if ((e = (call)) != cudaSuccess) return e;                                           \
     } while (0)
 
-// One query: the forward sweep, then the levels k = N-1..0.  *status gets the first
-// device status (CG or Newton failure); the call synchronises on s for the CG checks.
+// Loop control of a level's per-anchor CG, a conditional while node of a CUDA graph.
+// cnt: [0] anchors that iterated on in the last pass (k_anc_cg counts them), [1] device
+// status, [2] passes of the current loop, [3] passes of the whole call.
+__global__ void k_anc_loop_reset(int *cnt, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    cnt[0] = 0;
+    cnt[2] = 0;
+    cudaGraphSetConditional(h, 1u);
+}
+
+// After a pass: go on while some anchor is still iterating and fewer than max_iter passes
+// ran.
+__global__ void k_anc_loop_next(int *cnt, int max_iter, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    const int active = cnt[0], passes = cnt[2] + 1;
+    cnt[0] = 0;
+    cnt[2] = passes;
+    cnt[3] += 1;
+    cudaGraphSetConditional(h, (active > 0 && passes < max_iter) ? 1u : 0u);
+}
+
+// One query, enqueued on s, which must be capturing into a CUDA graph: the forward sweep,
+// then the levels k = N-1..0, each level's CG passes as a conditional while node whose
+// body is captured on the stream b.  The device status accumulates in cnt[1].
 // Kb: particles per anchor's regression (the cyclic window; Kb = M: all of them).
 template <typename Real>
-cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
-                      uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
-                      int *status, int *host_cnt, long long Kb)
+cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
+                     uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
+                     cudaStream_t b, long long Kb)
 {
     cudaError_t e;
     Params p = params_of(Pb, L, seed);
@@ -712,8 +737,7 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
     double *pn = reinterpret_cast<double *>(ws + L.pn), *an = reinterpret_cast<double *>(ws + L.an);
     double *cs = reinterpret_cast<double *>(ws + L.cs);
     Anchor *st = reinterpret_cast<Anchor *>(ws + L.st);
-    int *cnt = reinterpret_cast<int *>(ws + L.cnt);   // [0] active anchors, [1] status
-    ANC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
+    int *cnt = reinterpret_cast<int *>(ws + L.cnt);
     k_anc_terminal<Real><<<M, 128, 0, s>>>(p, x0, sidx, P, Y);
     ANC_TRY(cudaGetLastError());
     const dim3 cgrid((M + 127) / 128, L.nrc);
@@ -728,8 +752,8 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
     if (fused && Kb < M) ANC_TRY(cudaMemsetAsync(T, 0, (size_t)M * M * sizeof(Real), s));
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
-        const double a = (double)k / (double)(k + 1), b = p.sigma * std::sqrt(p.dt * a);
-        k_anc_step<Real><<<152 * 8, 256, 0, s>>>(p, k, sidx, a, b, P, A);
+        const double a = (double)k / (double)(k + 1), bb = p.sigma * std::sqrt(p.dt * a);
+        k_anc_step<Real><<<152 * 8, 256, 0, s>>>(p, k, sidx, a, bb, P, A);
         ANC_TRY(cudaGetLastError());
         k_anc_rows<Real><<<M, 128, 0, s>>>(p, P, A, Y, pn, an, YP);
         ANC_TRY(cudaGetLastError());
@@ -742,28 +766,60 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         k_anc_setup<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S,
                                                            rhs, x, r, pv, V);
         ANC_TRY(cudaGetLastError());
-        for (int it = 0; it < p.cg_max_iter; ++it) {
-            const bool check = it % kCheckEvery == kCheckEvery - 1 || it + 1 == p.cg_max_iter;
-            if (check) ANC_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));   // counts this pass
+        // the CG passes: a conditional while node (body on b) that repeats while some anchor
+        // iterates on and fewer than cg_max_iter passes ran
+        {
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *ed = nullptr;
+            size_t nd = 0;
+            ANC_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &ed, &nd));
+            if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+            cudaGraphConditionalHandle h;
+            ANC_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            k_anc_loop_reset<<<1, 32, 0, s>>>(cnt, h);
+            ANC_TRY(cudaGetLastError());
+            ANC_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &ed, &nd));
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            ANC_TRY(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+            ANC_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                        cudaStreamSetCaptureDependencies));
+            ANC_TRY(cudaStreamBeginCaptureToGraph(b, np.conditional.phGraph_out[0], nullptr, nullptr,
+                                                  0, cudaStreamCaptureModeRelaxed));
+            cudaError_t eb = cudaSuccess;
             if (fused) {   // T and its column sums straight from the product's epilogue
                 if constexpr (sizeof(Real) == 4)
-                    ANC_TRY((gemm_tc<false>(M, M, ld, ld, P, ld, V, ld,
-                                            TcColumnsEpi{W, T, st, cs, M}, cnt + 1, s, band)));
+                    eb = gemm_tc<false>(M, M, ld, ld, P, ld, V, ld, TcColumnsEpi{W, T, st, cs, M},
+                                        cnt + 1, b, band);
             } else {
-                ANC_TRY((gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, s, band)));   // U = P V^T
-                k_anc_columns<Real><<<cgrid, 128, 0, s>>>(p, 1, 0.0, Kb, G1, pn, an, Y, W, T, st, cs);
-                ANC_TRY(cudaGetLastError());
+                eb = gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, b, band);   // U = P V^T
+                if (eb == cudaSuccess) {
+                    k_anc_columns<Real><<<cgrid, 128, 0, b>>>(p, 1, 0.0, Kb, G1, pn, an, Y, W, T, st, cs);
+                    eb = cudaGetLastError();
+                }
             }
-            ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, s, band)));   // T^T P
-            k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, s>>>(
-                p, fused ? nrc_fused : L.nrc, fused ? dev::kTcBM : kRowChunk, band, L.nsplit, A,
-                G2, cs, S, st, x, r, pv, q, V, cnt);
-            ANC_TRY(cudaGetLastError());
-            if (check) {
-                ANC_TRY(cudaMemcpyAsync(host_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-                ANC_TRY(cudaStreamSynchronize(s));
-                if (*host_cnt == 0) break;   // every anchor converged (or failed)
+            if (eb == cudaSuccess)
+                eb = gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, b, band);   // T^T P
+            if (eb == cudaSuccess) {
+                k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, b>>>(
+                    p, fused ? nrc_fused : L.nrc, fused ? dev::kTcBM : kRowChunk, band, L.nsplit, A,
+                    G2, cs, S, st, x, r, pv, q, V, cnt);
+                eb = cudaGetLastError();
             }
+            if (eb == cudaSuccess) {
+                k_anc_loop_next<<<1, 32, 0, b>>>(cnt, p.cg_max_iter, h);
+                eb = cudaGetLastError();
+            }
+            cudaGraph_t ended = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(b, &ended);
+            if (eb != cudaSuccess) return eb;
+            if (ee != cudaSuccess) return ee;
         }
         k_anc_newton<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, t_k, x0, A, S, x, st, Yn, cnt + 1);
         ANC_TRY(cudaGetLastError());
@@ -771,11 +827,119 @@ cudaError_t solve_one(const fbsde_problem *Pb, const Lay &L, const double *x0, u
         std::swap(Y, Yn);
     }
     k_anc_output<<<1, 256, 0, s>>>(M, L.d, Y, x, u0, grad);
-    ANC_TRY(cudaGetLastError());
-    ANC_TRY(cudaMemcpyAsync(host_cnt, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ANC_TRY(cudaStreamSynchronize(s));
-    if (*host_cnt && !*status) *status = *host_cnt;
+    return cudaGetLastError();
+}
+
+// Every query of a call, enqueued on the capturing stream s (bodies on b): the counters and
+// the status word are cleared once, then the queries run one after the other on the
+// shared workspace.
+cudaError_t emit_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t Q,
+                      const double *x0, uint64_t seed, uint32_t solve_index0, double *u0,
+                      double *grad_u0, char *ws, cudaStream_t s, cudaStream_t b)
+{
+    cudaError_t e;
+    ANC_TRY(cudaMemsetAsync(ws + L.cnt, 0, 4 * sizeof(int), s));
+    for (int q = 0; q < Q; ++q) {
+        const double *xq = x0 + (size_t)q * P->d;
+        double *gq = grad_u0 ? grad_u0 + (size_t)q * P->d : nullptr;
+        e = P->precision == FBSDE_FP32
+                ? emit_one<float>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K)
+                : emit_one<double>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+// Instantiated graphs of whole calls, keyed by device and the bytes of every argument (an
+// eager call with the same arguments replays its graph).  Least-recently used entries beyond
+// kAncCacheSize are destroyed once their last launch has completed; the cache is never
+// freed, so no CUDA call runs from a static destructor at process exit.
+constexpr size_t kAncCacheSize = 8;
+struct AncGraph {
+    int dev;
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec;
+    cudaEvent_t last;
+};
+struct AncCache {
+    std::mutex mu;
+    std::list<AncGraph> lru;
+    cudaStream_t cap[64] = {}, body[64] = {};
+};
+AncCache *g_anc = new AncCache();
+
+template <typename T> void put(std::vector<unsigned char> &k, const T &v)
+{
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t Q,
+                        const double *x0, uint64_t seed, uint32_t solve_index0, double *u0,
+                        double *grad_u0, char *ws, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_anc->mu);
+    if (!g_anc->cap[dev]) {
+        if ((e = cudaStreamCreateWithFlags(&g_anc->cap[dev], cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamCreateWithFlags(&g_anc->body[dev], cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive)   // the caller is capturing: become part of it
+        return emit_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0, ws, s, g_anc->body[dev]);
+    std::vector<unsigned char> key;
+    put(key, *P);
+    put(key, K);
+    put(key, Q);
+    put(key, x0);
+    put(key, seed);
+    put(key, solve_index0);
+    put(key, u0);
+    put(key, grad_u0);
+    put(key, ws);
+    auto it = g_anc->lru.begin();
+    for (; it != g_anc->lru.end(); ++it)
+        if (it->dev == dev && it->key == key) break;
+    if (it == g_anc->lru.end()) {
+        cudaStream_t c = g_anc->cap[dev];
+        if ((e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        const cudaError_t ec =
+            emit_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0, ws, c, g_anc->body[dev]);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c, &g);
+        if (ec != cudaSuccess || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return ec != cudaSuccess ? ec : (e != cudaSuccess ? e : cudaErrorUnknown);
+        }
+        AncGraph a{dev, key, nullptr, nullptr};
+        e = cudaGraphInstantiate(&a.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&a.last, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaGraphExecDestroy(a.exec);
+            return e;
+        }
+        g_anc->lru.push_front(a);
+        while (g_anc->lru.size() > kAncCacheSize) {
+            AncGraph &old = g_anc->lru.back();
+            cudaEventSynchronize(old.last);
+            cudaGraphExecDestroy(old.exec);
+            cudaEventDestroy(old.last);
+            g_anc->lru.pop_back();
+        }
+        it = g_anc->lru.begin();
+    } else if (it != g_anc->lru.begin()) {
+        g_anc->lru.splice(g_anc->lru.begin(), g_anc->lru, it);
+        it = g_anc->lru.begin();
+    }
+    if ((e = cudaGraphLaunch(it->exec, s)) != cudaSuccess) return e;
+    return cudaEventRecord(it->last, s);
 }
 
 }  // namespace
@@ -813,20 +977,26 @@ int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double
     if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAl))
         return FBSDE_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    char *ws = static_cast<char *>(workspace);
-    int status = FBSDE_OK, host_cnt = 0;
-    for (int q = 0; q < Q; ++q) {
-        const double *xq = x0 + (size_t)q * P->d;
-        double *gq = grad_u0 ? grad_u0 + (size_t)q * P->d : nullptr;
-        const cudaError_t e =
-            P->precision == FBSDE_FP32
-                ? solve_one<float>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, &status,
-                                   &host_cnt, K)
-                : solve_one<double>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, &status,
-                                    &host_cnt, K);
-        if (e != cudaSuccess) return FBSDE_ERR_CUDA;
-    }
-    return status;
+    const cudaError_t e = launch_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0,
+                                      static_cast<char *>(workspace), s);
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
+int fbsde_anchored_diagnostics(const fbsde_problem *P, const void *workspace, fbsde_diag *out,
+                               fbsde_stream_t stream)
+{
+    Lay L;
+    if (!lay(P, L) || !workspace || !out) return FBSDE_ERR_ARG;
+    int h[4] = {0, 0, 0, 0};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(h, static_cast<const char *>(workspace) + L.cnt, sizeof(h),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    std::memset(out, 0, sizeof(*out));
+    out->status = h[1];
+    out->cg_iters_total = h[3];
+    return FBSDE_OK;
 }
 
 }  // extern "C"

@@ -75,7 +75,8 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_solve_noalloc", "fbsde_adjoint", "fbsde_adjoint_workspace_bytes",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
-           "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch"]
+           "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch",
+           "fbsde_anchored_diagnostics"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 13
 FBSDE_MAX_D = 16384
@@ -130,6 +131,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_solve_anchored.restype = C.c_int
         lib.fbsde_solve_batch.argtypes = [P, C.c_int64, I32, V, U64, U32, V, V, V, SZ, V]
         lib.fbsde_solve_batch.restype = C.c_int
+        lib.fbsde_anchored_diagnostics.argtypes = [P, V, C.POINTER(fbsde_diag), V]
+        lib.fbsde_anchored_diagnostics.restype = C.c_int
         lib.fbsde_adjoint_workspace_bytes.argtypes = [P, I32]
         lib.fbsde_adjoint_workspace_bytes.restype = SZ
         lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
@@ -231,7 +234,8 @@ def fbsde_anchored_workspace_bytes(problem: fbsde_problem) -> int:
 
 def fbsde_solve_anchored(problem: fbsde_problem, Q: int, x0, seed: int, solve_index0: int,
                          u0, grad_u0, workspace, stream=None) -> int:
-    """Algorithm 1 with one regression per particle anchor (blocking call)."""
+    """Algorithm 1 with one regression per particle anchor (asynchronous on the stream;
+    the device status through fbsde_anchored_diagnostics)."""
     return int(load_library().fbsde_solve_anchored(
         C.byref(problem), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
         _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
@@ -240,11 +244,19 @@ def fbsde_solve_anchored(problem: fbsde_problem, Q: int, x0, seed: int, solve_in
 
 def fbsde_solve_batch(problem: fbsde_problem, K: int, Q: int, x0, seed: int, solve_index0: int,
                       u0, grad_u0, workspace, stream=None) -> int:
-    """Algorithm 1 per anchor over a batch of K particles (cyclic window; blocking call)."""
+    """Algorithm 1 per anchor over a batch of K particles (cyclic window; asynchronous)."""
     return int(load_library().fbsde_solve_batch(
         C.byref(problem), int(K), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
         _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
         _stream(stream)))
+
+
+def fbsde_anchored_diagnostics(problem: fbsde_problem, workspace, stream=None) -> fbsde_diag:
+    out = fbsde_diag()
+    check(load_library().fbsde_anchored_diagnostics(C.byref(problem), _ptr(workspace),
+                                                    C.byref(out), _stream(stream)),
+          "fbsde_anchored_diagnostics")
+    return out
 
 
 def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0,
@@ -260,12 +272,13 @@ def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0,
     u = torch.empty(Q, dtype=torch.float64, device=x0.device)
     g = torch.empty(Q, problem.d, dtype=torch.float64, device=x0.device)
     if K is None:
-        st, name = fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws), "fbsde_solve_anchored"
+        check(fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws),
+              "fbsde_solve_anchored")
     else:
-        st, name = fbsde_solve_batch(problem, K, Q, x0, seed, solve_index0, u, g, ws), "fbsde_solve_batch"
-    if st not in (FBSDE_OK, FBSDE_ERR_CG, FBSDE_ERR_NEWTON, FBSDE_ERR_NONFINITE):
-        check(st, name)
-    return {"u0": u, "grad": g, "status": st}
+        check(fbsde_solve_batch(problem, K, Q, x0, seed, solve_index0, u, g, ws),
+              "fbsde_solve_batch")
+    dg = fbsde_anchored_diagnostics(problem, ws)
+    return {"u0": u, "grad": g, "status": int(dg.status), "cg_passes": int(dg.cg_iters_total)}
 
 
 def fbsde_adjoint_workspace_bytes(problem: fbsde_problem, Q: int) -> int:

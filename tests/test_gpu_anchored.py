@@ -160,3 +160,55 @@ def test_banded_products_match_oracle(prec, tol, M, K):
     from paper_2510_02635_gb300 import fbsde as fb
     out, refs, *_ = _run(fb, "ac_manufactured", 24, M, 2, prec, {}, Q=1, K=K)
     _check(out, refs, tol)
+
+
+@pytest.mark.parametrize("prec,M", [("fp64", 300), ("fp32", 1100)])
+def test_per_anchor_call_is_asynchronous_and_capturable(prec, M):
+    """The call enqueues its work and returns: captured by the caller into a CUDA graph (no
+    host synchronisation may occur during capture) and replayed, it gives the bits of the
+    eager call, which replays its own cached graph.  M = 1100 in FP32 takes the tensor-core
+    products with the fused column pass inside the conditional CG loop."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    d, N, Q, seed = 24, 3, 2, 5
+    x0 = torch.tensor(np.random.default_rng(8).normal(scale=0.4, size=(Q, d)), device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, prec,
+                        cg_tol=1e-13 if prec == "fp64" else 1e-7, cg_max_iter=1000)
+    ws = torch.empty(fb.fbsde_anchored_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    u = torch.empty(Q, dtype=torch.float64, device="cuda")
+    g = torch.empty(Q, d, dtype=torch.float64, device="cuda")
+    fb.check(fb.fbsde_solve_anchored(p, Q, x0, seed, 0, u, g, ws))
+    torch.cuda.synchronize()
+    assert fb.fbsde_anchored_diagnostics(p, ws).status == 0
+    u_ref, g_ref = u.clone(), g.clone()
+    fb.check(fb.fbsde_solve_anchored(p, Q, x0, seed, 0, u, g, ws))   # the cached graph
+    torch.cuda.synchronize()
+    assert torch.equal(u, u_ref) and torch.equal(g, g_ref)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+        fb.check(fb.fbsde_solve_anchored(p, Q, x0, seed, 0, u, g, ws,
+                                         stream=torch.cuda.current_stream()))
+    for _ in range(2):
+        u.zero_()
+        g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(u, u_ref) and torch.equal(g, g_ref)
+    assert fb.fbsde_anchored_diagnostics(p, ws).status == 0
+
+
+def test_per_anchor_status_reports_exhausted_cg():
+    """Three CG passes per level, far from the tolerance: the call itself returns
+    FBSDE_OK (it only enqueues), and the device status read afterwards is FBSDE_ERR_CG, with
+    three passes per level and query."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    d, M, N, Q = 16, 200, 3, 2
+    x0 = torch.zeros(Q, d, dtype=torch.float64, device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, "fp64", cg_tol=1e-15,
+                        cg_max_iter=3)
+    ws = torch.empty(fb.fbsde_anchored_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    u = torch.empty(Q, dtype=torch.float64, device="cuda")
+    assert fb.fbsde_solve_anchored(p, Q, x0, 1, 0, u, None, ws) == fb.FBSDE_OK
+    dg = fb.fbsde_anchored_diagnostics(p, ws)
+    assert dg.status == fb.FBSDE_ERR_CG
+    assert dg.cg_iters_total == 3 * N * Q
