@@ -296,10 +296,11 @@ def _events_ms(fn, repeats: int) -> float:
     return ev0.elapsed_time(ev1) / repeats
 
 
-def extra_batched(sample: int = 32) -> dict:
+def extra_batched(sample: int = 128) -> dict:
     """The 512-instance uneven batch in one autotuned FP32 plan (one graph launch per
-    step), and on its first `sample` instances: that batched FP32 plan vs the FP64 form
-    solving the same instances one at a time (one single-instance plan each, launched
+    step), and on a stratified sample of `sample` instances (every fourth instance in the
+    order of (d, M): every size class, up to d = 10^4): that batched FP32 plan vs the FP64
+    form solving the same instances one at a time (one single-instance plan each, launched
     and completed in turn; capture time excluded on both sides)."""
     import numpy as np
     import torch
@@ -330,16 +331,20 @@ def extra_batched(sample: int = 32) -> dict:
                  for w, c in zip(inst, cg))
     batch.close()
     units_full = sum(w.M * w.d * w.N for w in inst)
-    sub, subx = inst[:sample], x0s[:sample]
+    order = sorted(range(len(inst)), key=lambda i: (inst[i].d, inst[i].M, i))
+    pick = sorted(order[::max(1, len(inst) // sample)])
+    sub, subx = [inst[i] for i in pick], [x0s[i] for i in pick]
     b32 = autotune.Batch(sub, subx, table)
     ms32 = _events_ms(b32.launch, 2)
     u32, g32 = b32.results()
     b32.close()
-    inst64 = W.batch_instances(precision="fp64")[:sample]
+    all64 = W.batch_instances(precision="fp64")
+    inst64 = [all64[i] for i in pick]
     plans = []
-    for i, (w, x0) in enumerate(zip(inst64, subx)):
+    for w, x0 in zip(inst64, subx):
         plans.append(fbsde.Plan([{"problem": autotune.problem_of(w), "Q": 1, "seed": w.seed,
-                                  "x0": torch.tensor(x0, device="cuda"), "solve_index0": i}]))
+                                  "x0": torch.tensor(x0, device="cuda"),
+                                  "solve_index0": w.extra["index"]}]))
 
     def seq64():
         for pl in plans:
@@ -366,7 +371,9 @@ def extra_batched(sample: int = 32) -> dict:
             "unit": UNIT, "ms_per_batch": ms_full, "device_status": status,
             "plan_create_s": create_s, "autotune_s": tune_s, "cg_iters_total": sum(cg),
             "algorithmic_gb": nbytes / 1e9, "effective_gbs": nbytes / (ms_full * 1e-3) / 1e9,
-            "speedup_sample": {"instances": sample, "fp32_batched_ms": ms32,
+            "speedup_sample": {"instances": len(pick), "selection": "every 4th instance in "
+                               "the order of (d, M)", "max_d": max(w.d for w in sub),
+                               "fp32_batched_ms": ms32,
                                "fp64_per_instance_ms": ms64, "ratio": ms64 / ms32,
                                "fp64_routed": sum(1 for w in sub if w.precision == "fp64"),
                                "fp32_value": units_sub / (ms32 * 1e-3),

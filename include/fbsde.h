@@ -47,7 +47,8 @@ typedef struct CUstream_st *fbsde_stream_t; /* the same handle as cudaStream_t *
 
 #define FBSDE_ABI_VERSION 2
 #define FBSDE_MAX_D 16384 /* largest dimension d accepted */
-#define FBSDE_MAX_D_FP64 8192 /* largest d of the FP64 path (one 16-warp team per row) */
+#define FBSDE_MAX_D_FP64 10240 /* largest d of the FP64 path (one team of at most 10 warps
+                                  of 16 chunks per thread per row in the product kernel) */
 
 typedef enum {
     FBSDE_OK = 0,

@@ -17,7 +17,9 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Team geometry: a row of nch 16-byte chunks is covered by tw warps holding vpt
-// chunks per thread; narrow rows use one warp per row and 8 rows per CTA.
+// chunks per thread; narrow rows use one warp per row and 8 rows per CTA.  Rows of more
+// than 4096 chunks (FP64 rows beyond 8192 values) take 16 chunks per thread, so that their
+// team stays within 16 warps.
 bool choose_team(int nch, int &tw, int &vpt, int &teams)
 {
     constexpr int vmax = 8;
@@ -25,9 +27,12 @@ bool choose_team(int nch, int &tw, int &vpt, int &teams)
         tw = 1;
         vpt = 1;
         while (32 * vpt < nch) vpt *= 2;
-    } else {
+    } else if (nch <= 16 * 32 * vmax) {
         vpt = vmax;
         tw = (nch + 32 * vmax - 1) / (32 * vmax);
+    } else {
+        vpt = 2 * vmax;
+        tw = (nch + 32 * 2 * vmax - 1) / (32 * 2 * vmax);
     }
     if (32 * tw > 512) return false;
     teams = std::max(1, 256 / (32 * tw));
@@ -43,7 +48,8 @@ int check_problem(const fbsde_problem *P, int32_t Q, bool check_theta)
         return FBSDE_ERR_ARG;
     if (P->kind == FBSDE_HJB_LOGQUAD && P->sig1 != 0.0) return FBSDE_ERR_ARG;
     if (P->precision != FBSDE_FP32 && P->precision != FBSDE_FP64) return FBSDE_ERR_ARG;
-    if (P->d < 1 || P->d > FBSDE_MAX_D) return FBSDE_ERR_ARG;
+    if (P->d < 1 || P->d > (P->precision == FBSDE_FP64 ? FBSDE_MAX_D_FP64 : FBSDE_MAX_D))
+        return FBSDE_ERR_ARG;
     if (P->N < 1 || P->M < 2 || P->M > (int64_t)1 << 31) return FBSDE_ERR_ARG;
     if (!(P->sigma > 0.0) || !std::isfinite(P->sigma)) return FBSDE_ERR_ARG;
     if (!(P->T > 0.0) || !std::isfinite(P->T)) return FBSDE_ERR_ARG;

@@ -210,6 +210,11 @@ cudaError_t Launch<Real>::matvec(const Params &p, const Layout &L, cudaStream_t 
     case 4: return launch_matvec<Real, 4, false>(p, L, s);
     case 8: return wide ? launch_matvec<Real, 8, true>(p, L, s)
                         : launch_matvec<Real, 8, false>(p, L, s);
+    case 16:   // FP64 rows of 8193 to 10240 values: teams of 9 or 10 warps
+        if constexpr (sizeof(Real) == 8) {
+            if (!wide) return launch_matvec<Real, 16, false>(p, L, s);
+        }
+        return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }

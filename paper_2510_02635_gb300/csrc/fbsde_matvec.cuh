@@ -154,13 +154,19 @@ __global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matv
         const int team = ct / tthreads, tl = ct - team * tthreads, wt = tl >> 5;
         const Real *pv = ws.vR(s, 0);
         const Real *wv = ws.w(s);
-        Chunk<Real> acc[VPT], pc[VPT];
+        // the operand r: in registers, except with 16 chunks per thread (the widest FP64
+        // rows), where it is read through L1 for every row (it is the same for all rows)
+        constexpr bool kOpL1 = VPT > 8;
+        constexpr int kOpRegs = kOpL1 ? 1 : VPT;
+        Chunk<Real> acc[VPT], pc[kOpRegs];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             zero(acc[v]);
-            const int c = tl + tthreads * v;
-            if (c < nch) pc[v] = ldg_chunk(pv + c * E);
-            else zero(pc[v]);
+            if (!kOpL1) {
+                const int c = tl + tthreads * v;
+                if (c < nch) pc[v] = ldg_chunk(pv + c * E);
+                else zero(pc[v]);
+            }
         }
         int phase = 0;
         for (long long i = 0; i < nst; ++i) {
@@ -176,18 +182,26 @@ __global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matv
                 const Real wrow = wv[row0 + rr];
                 // narrow teams keep their chunks of the row in registers between the dot
                 // product and the weighted sum (one shared-memory read of the row instead
-                // of two); the 16-warp teams of the widest rows have no registers to spare
-                constexpr int kHeld = WIDE ? 1 : VPT;
+                // of two); the 16-warp teams of the widest rows, and the 16 chunks per
+                // thread of the widest FP64 rows, have no registers to spare
+                constexpr bool kReread = WIDE || VPT > 8;
+                constexpr int kHeld = kReread ? 1 : VPT;
                 Chunk<Real> dl[kHeld];
                 Real t = Real(0);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     const int c = tl + tthreads * v;
-                    Chunk<Real> &x = dl[WIDE ? 0 : v];
-                    if (c < nch) x = ld_chunk(row + c * E);
-                    else zero(x);
+                    Chunk<Real> &x = dl[kReread ? 0 : v];
+                    Chunk<Real> &o = pc[kOpL1 ? 0 : v];
+                    if (c < nch) {
+                        x = ld_chunk(row + c * E);
+                        if (kOpL1) o = ldg_chunk(pv + c * E);
+                    } else {
+                        zero(x);
+                        if (kOpL1) zero(o);
+                    }
 #pragma unroll
-                    for (int e = 0; e < E; ++e) t += x.v[e] * pc[v].v[e];
+                    for (int e = 0; e < E; ++e) t += x.v[e] * o.v[e];
                 }
 #pragma unroll
                 for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -204,8 +218,8 @@ __global__ void __launch_bounds__(WIDE ? 544 : (VPT >= 8 ? 352 : 288), 1) k_matv
                 for (int v = 0; v < VPT; ++v) {
                     const int c = tl + tthreads * v;
                     if (c < nch) {
-                        if (WIDE) dl[0] = ld_chunk(row + c * E);
-                        const Chunk<Real> &x = dl[WIDE ? 0 : v];
+                        if (kReread) dl[0] = ld_chunk(row + c * E);
+                        const Chunk<Real> &x = dl[kReread ? 0 : v];
 #pragma unroll
                         for (int e = 0; e < E; ++e) acc[v].v[e] += coef * x.v[e];
                     }

@@ -80,7 +80,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 13
 FBSDE_MAX_D = 16384
-FBSDE_MAX_D_FP64 = 8192
+FBSDE_MAX_D_FP64 = 10240
 FBSDE_PROFILED_EAGER_PASSES = 48   # the header constant of the same name
 
 _lock = threading.Lock()

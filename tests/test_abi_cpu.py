@@ -75,7 +75,7 @@ def test_workspace_sizing(lib):
 @pytest.mark.parametrize("bad", [dict(d=0), dict(d=fbsde.FBSDE_MAX_D + 1), dict(M=1),
                                  dict(N=0), dict(sigma=0.0), dict(sigma=math.nan), dict(T=-1.0),
                                  dict(cg_tol=0.0), dict(ridge_rel=-1.0),
-                                 dict(precision="fp64", d=9000)])
+                                 dict(precision="fp64", d=10241)])
 def test_invalid_problems_are_rejected(lib, bad):
     p = _prob(**bad)
     assert fbsde.fbsde_workspace_bytes(p, 1) == 0

@@ -51,7 +51,8 @@ SHAPES = [
     ("ac_manufactured", 1, 37, 3, 3),
     ("cos_linear_test", 3, 9, 2, 5),
     ("ac_manufactured", 4096, 48, 2, 1),     # FP64: 2048 row chunks, 8-warp team
-    ("ac_manufactured", 10240, 48, 2, 1),    # FP32: 2560 row chunks, one 10-warp team
+    ("ac_manufactured", 10240, 48, 2, 1),    # FP32: 2560 row chunks, one 10-warp team;
+                                             # FP64: 5120 chunks, 10 warps of 16 chunks
     ("ac_manufactured", 10241, 48, 2, 1),    # FP32: 2561 chunks, 11-warp team (544 threads)
 ]
 
@@ -59,8 +60,8 @@ SHAPES = [
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("kind,d,M,N,Q", SHAPES)
 def test_edge_shapes_match_oracle(kind, d, M, N, Q, prec):
-    if prec == "fp64" and d > 8192:
-        pytest.skip("FP64 rows are limited to d <= 8192")
+    if prec == "fp64" and d > 10240:
+        pytest.skip("FP64 rows are limited to d <= 10240")
     extra = {"c1": 0.3} if kind == "cos_linear_test" else {}
     _check(_w(kind, d, M, N, Q, prec, **_few_particles(d, M), **extra))
 
@@ -70,7 +71,7 @@ def test_more_queries_than_ctas():
     _check(_w("ac_manufactured", 5, 16, 2, 700, "fp32"), queries=[0, 1, 350, 699])
 
 
-@pytest.mark.parametrize("prec,d", [("fp32", 16384), ("fp64", 8192)])
+@pytest.mark.parametrize("prec,d", [("fp32", 16384), ("fp64", 8192), ("fp64", 10240)])
 def test_largest_dimension(prec, d):
     _check(_w("ac_manufactured", d, 40, 2, 1, prec, **_few_particles(d, 40)))
 
@@ -78,6 +79,6 @@ def test_largest_dimension(prec, d):
 def test_dimension_beyond_the_limit_is_rejected():
     from paper_2510_02635_gb300 import fbsde
     fbsde.load_library()
-    for prec, d in (("fp32", 16385), ("fp64", 8193)):
+    for prec, d in (("fp32", 16385), ("fp64", 10241)):
         p = fbsde.make_problem("ac_manufactured", d, 2, 40, 1.0, 0.5, prec)
         assert fbsde.fbsde_workspace_bytes(p, 1) == 0
