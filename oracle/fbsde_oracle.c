@@ -810,10 +810,11 @@ done:
 /*
  * Algorithm 1 with one regression per particle anchor over a batch of K particles (the
  * random-batch reading of Remark 2.1, after Jin, Li and Liu 2020): for anchor m the batch
- * is the cyclic window j = (m + q) mod M, q = 0..K-1.  The particle paths are independent
- * and identically distributed and the window does not depend on them, so it is a random
- * batch in law; the Gaussian weights are normalised over the batch.  K = M is
- * orc_solve_anchored up to the order of the sums.
+ * is the cyclic window j = (m + q) mod M, q = 0..K-1.  The window does not depend on the
+ * positions, and the particle paths are independent and identically distributed, so its
+ * K - 1 particles other than the anchor's own path (q = 0, always in the batch) are a
+ * random sample of the cloud; the Gaussian weights are normalised over the batch.  K = M
+ * is orc_solve_anchored up to the order of the sums.
  */
 int orc_solve_batch(const orc_problem *P, int64_t K, const double *x0, uint64_t seed,
                     uint32_t solve_index, double *u0, double *grad_u0)
