@@ -568,8 +568,8 @@ cudaError_t run(Params p, const Layout &L, const double *x0, const double *theta
 // Algorithm 1 with Euler-Maruyama paths (2.7).  The forward sweep keeps the rows of the
 // levels s, 2s, .. (checkpoints) and of the last segment; on the way back the level-k rows
 // come from a checkpoint or the segment buffer (a segment is recomputed from its checkpoint
-// when the sweep enters it) and are copied into the row buffer, so every level's kernels
-// (and the cached CG-loop graph) see the same rows pointer.  Per level k: row sums
+// when the sweep enters it) and are copied into the row buffer by the row-sum kernel, so
+// every level's kernels (and the cached CG-loop graph) see the same rows pointer.  Per level k: row sums
 // (k_sde_rows), the kernel scale (k_sde_rho), the per-particle values and weights, the
 // moments and the regression set-up of level k - 1.
 template <typename Real>
@@ -597,7 +597,7 @@ cudaError_t run_sde(Params p, const Layout &L, const double *x0, const double *t
     int seg = (N - 1) / sq * sq;   // the segment whose levels the forward sweep left in place
     p.level = N;
     p.newton_level = -1;
-    FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, N, s));
+    FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, N, nullptr, s));
     FBSDE_TRY(FBSDE_K_PARTICLES, LR::sde_rho(p, L, s));
     FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
     if (p.tr_x_N || p.tr_y_N) FBSDE_TRY(FBSDE_K_TRACE, LR::trace_forward(p, L, s));
@@ -618,10 +618,8 @@ cudaError_t run_sde(Params p, const Layout &L, const double *x0, const double *t
             }
             seg = b;
         }
-        if ((e = cudaMemcpyAsync(p.delta, slot(k), slab, cudaMemcpyDeviceToDevice, s)) !=
-            cudaSuccess)
-            return e;
-        FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, k, s));
+        // the level's rows from their slot into the row buffer, with the row sums
+        FBSDE_TRY(FBSDE_K_UPDATE, LR::sde_rows(p, L, k, slot(k), s));
         FBSDE_TRY(FBSDE_K_PARTICLES, LR::sde_rho(p, L, s));
         FBSDE_TRY(FBSDE_K_PARTICLES, LR::particles(p, L, s));
         FBSDE_TRY(FBSDE_K_MOMENTS, LR::moments(p, L, s));

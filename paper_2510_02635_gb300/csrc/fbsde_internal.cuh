@@ -134,7 +134,8 @@ template <typename Real> struct Launch {
     static cudaError_t sde_anchor(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t sde_forward(const Params &p, const Layout &L, int k, const void *from,
                                    void *to, cudaStream_t s);
-    static cudaError_t sde_rows(const Params &p, const Layout &L, int k, cudaStream_t s);
+    static cudaError_t sde_rows(const Params &p, const Layout &L, int k, const void *src,
+                                cudaStream_t s);
     static cudaError_t sde_rho(const Params &p, const Layout &L, cudaStream_t s);
     static cudaError_t reduce(const Params &p, const Layout &L, int nvec, int dst0, int skip_done,
                               cudaStream_t s);

@@ -74,21 +74,29 @@ cudaError_t Launch<Real>::sde_forward(const Params &p, const Layout &L, int k, c
                                       void *to, cudaStream_t s)
 {
     if (k < 0 || k >= p.N || !to) return cudaErrorInvalidValue;
-    const long long n = (long long)L.Q * L.M * (L.ld * (long long)L.real_sz / 16);
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-    dev::k_sde_forward<Real><<<blocks, 256, 0, s>>>(p, k, static_cast<const Real *>(from),
-                                                   static_cast<Real *>(to));
+    const Real *src = static_cast<const Real *>(from);
+    Real *dst = static_cast<Real *>(to);
+    switch (L.seg_vpt) {
+    case 1: dev::k_sde_forward<Real, 1><<<L.row_blocks, 256, 0, s>>>(p, k, src, dst); break;
+    case 2: dev::k_sde_forward<Real, 2><<<L.row_blocks, 256, 0, s>>>(p, k, src, dst); break;
+    case 4: dev::k_sde_forward<Real, 4><<<L.row_blocks, 256, 0, s>>>(p, k, src, dst); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
+// Row sums of level k from the row buffer, or (src) from a stored level, copied into the
+// row buffer on the way.
 template <typename Real>
-cudaError_t Launch<Real>::sde_rows(const Params &p, const Layout &L, int k, cudaStream_t s)
+cudaError_t Launch<Real>::sde_rows(const Params &p, const Layout &L, int k, const void *src,
+                                   cudaStream_t s)
 {
     if (k < 1 || k > p.N) return cudaErrorInvalidValue;
+    const Real *sr = static_cast<const Real *>(src);
     switch (L.seg_vpt) {
-    case 1: dev::k_sde_rows<Real, 1><<<L.row_blocks, 256, 0, s>>>(p, k); break;
-    case 2: dev::k_sde_rows<Real, 2><<<L.row_blocks, 256, 0, s>>>(p, k); break;
-    case 4: dev::k_sde_rows<Real, 4><<<L.row_blocks, 256, 0, s>>>(p, k); break;
+    case 1: dev::k_sde_rows<Real, 1><<<L.row_blocks, 256, 0, s>>>(p, k, sr); break;
+    case 2: dev::k_sde_rows<Real, 2><<<L.row_blocks, 256, 0, s>>>(p, k, sr); break;
+    case 4: dev::k_sde_rows<Real, 4><<<L.row_blocks, 256, 0, s>>>(p, k, sr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -39,37 +39,46 @@ __global__ void __launch_bounds__(256) k_sde_anchor(Params p)
     }
 }
 
-// Euler-Maruyama step k -> k + 1 of every row (grid-stride over (query, particle, chunk));
-// from == nullptr: level 0 (Delta_0 = 0).  Padding (i >= d) stays zero.
-template <typename Real>
+// Euler-Maruyama step k -> k + 1 of every row; from == nullptr: level 0 (Delta_0 = 0).
+// One warp per (query, particle, row segment), the walk of k_update (no integer division
+// per item); padding (i >= d) stays zero.
+template <typename Real, int VPT>
 __global__ void __launch_bounds__(256) k_sde_forward(Params p, int k, const Real *from, Real *to)
 {
     constexpr int E = Chunk<Real>::E;
     const WS<Real> ws(p);
+    const int lane = threadIdx.x & 31;
     const int nch = p.ld / E;
-    const long long n = (long long)p.Q * p.M * nch;
     const Real sdt = (Real)sqrt(p.dt), dt = (Real)p.dt;
     const Real mu0 = (Real)p.mu0, mu1 = (Real)p.mu1, sg0 = (Real)p.sigma, sg1 = (Real)p.sig1;
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n;
-         it += (long long)gridDim.x * blockDim.x) {
-        const long long row = it / nch;
-        const int c = (int)(it - row * nch);
-        const int s = (int)(row / p.M);
-        const long long j = row - (long long)s * p.M;
-        const size_t off = (size_t)row * p.ld + (size_t)c * E;
-        Chunk<Real> dl;
-        if (from) dl = ld_chunk(from + off);
-        else zero(dl);
-        const Chunk<Real> xc = ldg_chunk(ws.vR(s, 2) + c * E);
-        const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, (uint32_t)j, (uint32_t)k,
-                                           p.solve0 + (uint32_t)s, p.key0, p.key1, p.d);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (RowItems w(p, (((unsigned long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5,
+                    (unsigned long long)nwarps);
+         w.s < (uint32_t)p.Q; w.next()) {
+        const int seg = (int)w.seg, s = (int)w.s;
+        const size_t row = (size_t)s * p.M + w.j;
+        const Real *src = from ? from + row * p.ld : nullptr;
+        Real *dst = to + row * p.ld;
+        const Real *x0r = ws.vR(s, 2);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const Real x = xc.v[e] + dl.v[e];
-            const Real v = dl.v[e] + (mu0 + mu1 * x) * dt + (sg0 + sg1 * x) * sdt * z.v[e];
-            dl.v[e] = c * E + e < p.d ? v : Real(0);
+        for (int v = 0; v < VPT; ++v) {
+            const int c = seg * 32 * VPT + lane + 32 * v;
+            if (c < nch) {
+                Chunk<Real> dl;
+                if (src) dl = ld_chunk(src + c * E);
+                else zero(dl);
+                const Chunk<Real> xc = ldg_chunk(x0r + c * E);
+                const Chunk<Real> z = normal_chunk((Chunk<Real> *)nullptr, c, w.j, (uint32_t)k,
+                                                   p.solve0 + (uint32_t)s, p.key0, p.key1, p.d);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const Real x = xc.v[e] + dl.v[e];
+                    const Real v2 = dl.v[e] + (mu0 + mu1 * x) * dt + (sg0 + sg1 * x) * sdt * z.v[e];
+                    dl.v[e] = c * E + e < p.d ? v2 : Real(0);
+                }
+                st_chunk(dst + c * E, dl);
+            }
         }
-        st_chunk(to + off, dl);
     }
 }
 
@@ -116,8 +125,10 @@ __device__ __forceinline__ void sde_terms(const Params &p, bool terminal, Real x
 // of level k - 1 (the regression level k's values feed), [3] g . Delta (g the starting
 // guess of that regression's solve), [4], [5] the feature sums (sde_terms; padding
 // excluded).
+// src != nullptr: the rows of level k are read from src (a stored level) and copied into
+// the row buffer on the way.
 template <typename Real, int VPT>
-__global__ void __launch_bounds__(256) k_sde_rows(Params p, int k)
+__global__ void __launch_bounds__(256) k_sde_rows(Params p, int k, const Real *src)
 {
     constexpr int E = Chunk<Real>::E;
     const WS<Real> ws(p);
@@ -130,14 +141,21 @@ __global__ void __launch_bounds__(256) k_sde_rows(Params p, int k)
          w.s < (uint32_t)p.Q; w.next()) {
         const int seg = (int)w.seg, s = (int)w.s;
         const long long j = w.j;
-        const Real *drow = ws.row(s, j);
+        Real *drow = ws.row(s, j);
+        const Real *srow = src ? src + ((size_t)s * p.M + j) * p.ld : nullptr;
         const Real *ar = ws.anchor(s, k - 1);
         Real acc[kSegSums] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int c = seg * 32 * VPT + lane + 32 * v;
             if (c < nch) {
-                const Chunk<Real> dl = ld_chunk(drow + c * E);
+                Chunk<Real> dl;
+                if (srow) {
+                    dl = ld_chunk(srow + c * E);
+                    st_chunk(drow + c * E, dl);
+                } else {
+                    dl = ld_chunk(drow + c * E);
+                }
                 const Chunk<Real> xc = ldg_chunk(ws.vR(s, 1) + c * E);   // alpha_x
                 const Chunk<Real> x0c = ldg_chunk(ws.vR(s, 2) + c * E);
                 const Chunk<Real> gc = ldg_chunk(ws.vR(s, 3) + c * E);

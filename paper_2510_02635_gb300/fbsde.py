@@ -574,6 +574,9 @@ def _main(argv=None) -> None:
                     help="run the launch profiler on the product kernel (the first "
                          "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
                          "one by one, outside CUDA graphs, e.g. for a kernel profiler)")
+    ap.add_argument("--mu0", type=float, default=0.0, help="drift mu0 + mu1 x_i")
+    ap.add_argument("--mu1", type=float, default=0.0)
+    ap.add_argument("--sig1", type=float, default=0.0, help="diffusion sigma + sig1 x_i")
     ap.add_argument("--time-family", default=None,
                     help="time the launches of one kernel family (e.g. step), or of "
                          "every family (all), with the library's launch profiler")
@@ -583,7 +586,8 @@ def _main(argv=None) -> None:
                       else np.zeros((a.Q, a.d)), device="cuda")
     theta = rng.uniform(0.5, 1.5, size=a.d) if a.kind in ("hjb_logquad", "affine_test") else None
     solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
-                    theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter)
+                    theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter, mu0=a.mu0,
+                    mu1=a.mu1, sig1=a.sig1)
     if a.time_products or a.time_family:
         fbsde_profile_start(1 << 20)
         if a.time_family != "all":
