@@ -118,7 +118,8 @@ typedef struct {
     double newton_tol;       /* Newton stops when |dY| <= newton_tol max(1,|Y|); 0 selects 1e-13 */
     int32_t ctas;            /* CTAs of one streaming pass over all Q queries (tiling of the
                                 particle clouds; results depend on it through the order of
-                                the partial sums); 0 selects 608                          */
+                                the partial sums); 0 selects 608; at most M / 32 CTAs
+                                per query are used                                       */
     int32_t reserved;        /* must be 0                                               */
     /* Forward SDE dX = mu(t,X) dt + sigma(t,X) dW of Sec. 2.1 with the componentwise affine
        coefficients mu_i(x) = mu0 + mu1 x_i and sigma(x) = diag(sigma + sig1 x_i).  With

@@ -44,7 +44,8 @@ constexpr int kSegSums = 6;   // per-row-segment sums of the row kernels (the fo
                               // rows use all six, the driftless ones the first four)
 constexpr int kFinThreads = 512;   // threads of the one-CTA-per-solve kernels
 constexpr int kTargetCtas = 608;   // default: 4 x 152 SMs, CTAs of one streaming pass over all queries
-constexpr int kMinRowsPerCta = 8;
+constexpr int kMinRowsPerCta = 32;   // rows of a streaming pass per CTA at least: fewer
+                                     // partial vectors for the reduction of small clouds
 constexpr int kRowBlocks = 152 * 8;  // grid of the row-segment kernels (grid-stride)
 constexpr int kStepMaxLd = 10240;    // widest FP32 row of the fused per-level step
 constexpr int kStepElems = 10240;    // particle-dims per stage of the fused step
