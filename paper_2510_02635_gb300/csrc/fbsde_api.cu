@@ -355,6 +355,8 @@ struct Rec {
         if ((e = (call)) != cudaSuccess) return e;                                           \
     } while (0)
 
+constexpr int kCgUnroll = 2;   // CG passes per iteration of the conditional while node
+
 // The CG loop captured into the graph being built on stream s: a reset kernel that sets
 // the loop condition, then a conditional while node whose body (product, reduction, CG
 // update) is captured on the stream `body`; k_cg_update keeps the condition at 1 while
@@ -390,9 +392,15 @@ cudaError_t cg_capture(const Params &p, const Layout &L, cudaStream_t s, cudaStr
     if ((e = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return e;
-    cudaError_t eb = LR::matvec(p, L, b);
-    if (eb == cudaSuccess) eb = LR::reduce(p, L, 1, 5, 1, b);
-    if (eb == cudaSuccess) eb = LR::cg_update(p, L, h, 1, b);
+    // kCgUnroll passes per iteration of the while node: each iteration of a conditional
+    // node costs a device-side launch of its body graph; passes after convergence exit at
+    // once (the kernels test the query's done flag), and every pass updates the condition
+    cudaError_t eb = cudaSuccess;
+    for (int u = 0; u < kCgUnroll && eb == cudaSuccess; ++u) {
+        eb = LR::matvec(p, L, b);
+        if (eb == cudaSuccess) eb = LR::reduce(p, L, 1, 5, 1, b);
+        if (eb == cudaSuccess) eb = LR::cg_update(p, L, h, 1, b);
+    }
     cudaGraph_t ended = nullptr;
     e = cudaStreamEndCapture(b, &ended);
     return eb != cudaSuccess ? eb : e;
