@@ -643,10 +643,11 @@ def run_gpu(args, rank: int, world: int) -> None:
     step_bytes = 8.0 * w.Q * w.M * w.d * (w.N - 1) + 4.0 * w.Q * w.M * w.d
     step_gbs = step_bytes / (step_ms * 1e-3) / 1e9
     # kernels the library launched one by one, plus those run inside the CG-loop graphs
-    # (one reset kernel per level and three per pass beyond the eager ones)
+    # (one reset kernel per level, and three per pass beyond the eager ones, the passes
+    # rounded up to the two per iteration of the loop)
     beyond = np.maximum(cg_iters.reshape(w.Q, w.N).max(axis=0) - eager, 0)
     launches = sum(v["launches"] for v in prof.values()) + \
-        args.steps * int(w.N + 3 * beyond.sum())
+        args.steps * int(w.N + 3 * (2 * ((beyond + 1) // 2)).sum())
 
     # ---- per-family split: one more solve, every launch bracketed (outside the timed region)
     fbsde.fbsde_profile_start(1 << 18)
@@ -726,7 +727,8 @@ def run_gpu(args, rank: int, world: int) -> None:
                          "kernel_ms_per_step": mv_ms_step},
             "kernels_ms_per_step": {k: v["total_ms"] for k, v in split.items()},
             "kernels_ms_note": "one extra solve after the timed region with every launch "
-                               "bracketed by events (the timed region brackets only matvec)",
+                               "bracketed by events (the timed region brackets only matvec "
+                               "and step)",
             "roofline_step": {"kernel": "step", "bound": "hbm", "achieved": step_gbs,
                               "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                               "frac": step_gbs / peak, "traffic": _step_traffic(w),
