@@ -6,9 +6,9 @@ particle) against the FP64 oracle of the same scheme, on identical seeded inputs
 FP64 path: the end point of the paths, Y_N, every level's alpha and alpha_x, u(0,x0) and
 grad u(0,x0) within 1e-10.  FP32 path: u within 1e-4 relative, grad within
 1e-4 max(|grad u|, |u|).  The cases span ragged d and M, several row teams (d > 1024),
-every kind of the problem table, N = 1 and N = 2 (no stored level, one segment slot), and
+every kind of the problem table, N = 1 and N = 2 (no stored level, one segment slot),
 N = 9, 10, 17 (checkpoints at s, 2s, .. with s = ceil(sqrt N); segments recomputed on the
-way back)."""
+way back), and rows of 10^4 and 10240 values."""
 import math
 
 import numpy as np
@@ -45,6 +45,10 @@ CASES = [
     ("cos_linear_test", 29, 211, 1, 1.0, 0.4, (0.1, 0.2, 0.1), {"c1": 0.4}),
     ("cubic_test", 24, 230, 3, 1.0, 0.3, (0.1, -0.2, 0.1), {"A": 0.5}),
     ("drift_quad", 12, 500, 17, 0.6, 0.5, (-0.2, -1.0, 0.3), {}),
+    # wide rows (several warps per row segment walk; FP64 at its largest d): with M < d the
+    # regression has rank M - 1, so the ridge is the mean eigenvalue (condition ~ d / M)
+    ("drift_ac", 10000, 160, 3, 0.5, 0.5, (0.1, -0.5, 0.2), {"ridge_rel": 1.0}),
+    ("drift_quad", 10240, 120, 2, 0.4, 0.5, (0.0, -0.3, 0.1), {"ridge_rel": 1.0}),
 ]
 
 
