@@ -298,7 +298,7 @@ __device__ __forceinline__ Real split_sum(const Real *X, size_t split, size_t ix
 // warp-only tree sums: on this part the FP64 pipe is a small fraction of the FP32 one, and
 // block-wide FP64 reductions repeated by every thread cost more than the element work.
 constexpr int kAncWarps = 8;
-template <int NV> __device__ __forceinline__ void warp_sums(double (&v)[NV])
+template <typename T, int NV> __device__ __forceinline__ void warp_sums(T (&v)[NV])
 {
 #pragma unroll
     for (int i = 0; i < NV; ++i)
@@ -306,13 +306,16 @@ template <int NV> __device__ __forceinline__ void warp_sums(double (&v)[NV])
         for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
 
-// Per anchor: S, rhs, lambda, and the CG start x = 0, r = p = rhs.
+// Per anchor: S, rhs, lambda, and the CG start x = 0, r = p = rhs.  The per-anchor
+// d-vectors (S, rhs, x, r, p, q) and their element arithmetic are in the stream precision:
+// on the FP32 path the CG passes then run on the FP32 pipe at half the bytes (the FP64 pipe
+// is a small fraction of it on this part); the scalars of each anchor stay FP64.
 template <typename Real>
 __global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc, int nsplit,
                                                               const Real *A, const Real *G2,
                                                               const Real *G3, const double *part,
-                                                              Anchor *st, double *S, double *rhs,
-                                                              double *x, double *r, double *pv,
+                                                              Anchor *st, Real *S, Real *rhs,
+                                                              Real *x, Real *r, Real *pv,
                                                               Real *V)
 {
     const int lane = threadIdx.x & 31;
@@ -329,20 +332,21 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc,
     }
     warp_sums(w);
     const double invW = 1.0 / w[0], cm = w[1] / w[0];
+    const Real invWr = (Real)invW, cmr = (Real)cm;
     const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // |S|^2, |rhs|^2, S . rhs, A . rhs
+    Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};   // |S|^2, |rhs|^2, S . rhs, A . rhs
     for (int i = lane; i < p.ld; i += 32) {
-        const double g2 = (double)split_sum(G2, split, o + i, nsplit) * invW;
-        const double g3 = (double)split_sum(G3, split, o + i, nsplit);
-        const double ai = (double)A[o + i];
-        const double sv = g2 - ai;
-        const double b = g3 * invW - cm * g2;
+        const Real g2 = split_sum(G2, split, o + i, nsplit) * invWr;
+        const Real g3 = split_sum(G3, split, o + i, nsplit);
+        const Real ai = A[o + i];
+        const Real sv = g2 - ai;
+        const Real b = g3 * invWr - cmr * g2;
         S[o + i] = sv;
         rhs[o + i] = b;
-        x[o + i] = 0.0;
+        x[o + i] = Real(0);
         r[o + i] = b;
         pv[o + i] = b;
-        V[o + i] = (Real)b;
+        V[o + i] = b;
         acc[0] += sv * sv;
         acc[1] += b * b;
         acc[2] += sv * b;
@@ -371,9 +375,9 @@ template <typename Real>
 __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, int rows_per_chunk,
                                                            dev::Band band, int nsplit,
                                                            const Real *A, const Real *G,
-                                                           const double *part, const double *S,
-                                                           Anchor *st, double *x, double *r,
-                                                           double *pv, double *q, Real *V,
+                                                           const double *part, const Real *S,
+                                                           Anchor *st, Real *x, Real *r,
+                                                           Real *pv, Real *q, Real *V,
                                                            int *active)
 {
     const int lane = threadIdx.x & 31;
@@ -389,45 +393,49 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
     }
     warp_sums(cs);
     const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
-    const double sp = a.sp, lam = a.lam, rr = a.rr;
-    double pq[1] = {0.0};
+    const double rr = a.rr;
+    const Real csr = (Real)cs[0], spr = (Real)a.sp, lamr = (Real)a.lam;
+    Real pq[1] = {Real(0)};
     for (int i = lane; i < p.ld; i += 32) {
-        const double g = (double)split_sum(G, split, o + i, nsplit);
-        const double qi = g - cs[0] * (double)A[o + i] - S[o + i] * sp + lam * pv[o + i];
+        const Real g = split_sum(G, split, o + i, nsplit);
+        const Real qi = g - csr * A[o + i] - S[o + i] * spr + lamr * pv[o + i];
         q[o + i] = qi;
         pq[0] += pv[o + i] * qi;
     }
     warp_sums(pq);
-    if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
+    const double pqd = (double)pq[0];
+    if (!(pqd > 0.0) || !isfinite(pqd)) {
         if (lane == 0) {
             a.done = 1;
             if (!(rr <= p.cg_tol2 * a.rhs2)) a.status = FBSDE_ERR_CG;
         }
         return;
     }
-    const double step = rr / pq[0];
-    double rn[1] = {0.0};
+    const double step = rr / pqd;
+    const Real stepr = (Real)step;
+    Real rn[1] = {Real(0)};
     for (int i = lane; i < p.ld; i += 32) {
-        x[o + i] += step * pv[o + i];
-        const double ri = r[o + i] - step * q[o + i];
+        x[o + i] += stepr * pv[o + i];
+        const Real ri = r[o + i] - stepr * q[o + i];
         r[o + i] = ri;
         rn[0] += ri * ri;
     }
     warp_sums(rn);
-    const double rr_new = rn[0], beta = rr_new / rr;
-    double b[2] = {0.0, 0.0};
+    const double rr_new = (double)rn[0], beta = rr_new / rr;
+    const Real betar = (Real)beta;
+    Real b[2] = {Real(0), Real(0)};
     for (int i = lane; i < p.ld; i += 32) {
-        const double pi = r[o + i] + beta * pv[o + i];
+        const Real pi = r[o + i] + betar * pv[o + i];
         pv[o + i] = pi;
-        V[o + i] = (Real)pi;
+        V[o + i] = pi;
         b[0] += S[o + i] * pi;
-        b[1] += (double)A[o + i] * pi;
+        b[1] += A[o + i] * pi;
     }
     warp_sums(b);
     if (lane == 0) {
         a.rr = rr_new;
-        a.sp = b[0];
-        a.ap = b[1];
+        a.sp = (double)b[0];
+        a.ap = (double)b[1];
         a.iters += 1;
         if (rr_new <= p.cg_tol2 * a.rhs2) {
             a.done = 1;
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
 template <typename Real>
 __global__ void __launch_bounds__(32 * kAncWarps) k_anc_newton(Params p, double t_k,
                                                                const double *x0, const Real *A,
-                                                               const double *S, const double *x,
+                                                               const Real *S, const Real *x,
                                                                Anchor *st, double *Ynew,
                                                                int *status)
 {
@@ -456,8 +464,8 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_newton(Params p, double 
     const size_t o = (size_t)m * p.ld;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // S . x, sum cos(x0 + A), sum x, |x|^2
     for (int i = lane; i < p.ld; i += 32) {
-        const double xi = x[o + i];
-        acc[0] += S[o + i] * xi;
+        const double xi = (double)x[o + i];
+        acc[0] += (double)S[o + i] * xi;
         if (i < p.d) acc[1] += (double)dev::cos_stream((Real)x0[i] + A[o + i]);
         acc[2] += xi;
         acc[3] += xi * xi;
@@ -479,7 +487,8 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_newton(Params p, double 
 }
 
 // u(0,x0) = mean of Y_0^m (fixed order) and grad u(0,x0) = x of anchor 0.
-__global__ void __launch_bounds__(256) k_anc_output(int M, int d, const double *Y, const double *x,
+template <typename Real>
+__global__ void __launch_bounds__(256) k_anc_output(int M, int d, const double *Y, const Real *x,
                                                     double *u0, double *grad)
 {
     __shared__ double sm[32];
@@ -488,7 +497,7 @@ __global__ void __launch_bounds__(256) k_anc_output(int M, int d, const double *
     bsum(acc, sm);
     if (threadIdx.x == 0) *u0 = acc[0] / M;
     if (grad)
-        for (int i = threadIdx.x; i < d; i += blockDim.x) grad[i] = x[i];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) grad[i] = (double)x[i];
 }
 
 }  // namespace anchored
@@ -549,12 +558,12 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.T = take(M * M * L.rs);
     L.G2 = take((size_t)L.nsplit * M * ld * L.rs);
     L.G3 = take((size_t)L.nsplit * M * ld * L.rs);
-    L.S = take(M * ld * 8);
-    L.rhs = take(M * ld * 8);
-    L.x = take(M * ld * 8);
-    L.r = take(M * ld * 8);
-    L.pv = take(M * ld * 8);
-    L.q = take(M * ld * 8);
+    L.S = take(M * ld * L.rs);
+    L.rhs = take(M * ld * L.rs);
+    L.x = take(M * ld * L.rs);
+    L.r = take(M * ld * L.rs);
+    L.pv = take(M * ld * L.rs);
+    L.q = take(M * ld * L.rs);
     L.Y = take(M * 8);
     L.Yn = take(M * 8);
     L.pn = take(M * 8);
@@ -730,9 +739,9 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
     Real *G1 = reinterpret_cast<Real *>(ws + L.G1), *W = reinterpret_cast<Real *>(ws + L.W);
     Real *T = reinterpret_cast<Real *>(ws + L.T);
     Real *G2 = reinterpret_cast<Real *>(ws + L.G2), *G3 = reinterpret_cast<Real *>(ws + L.G3);
-    double *S = reinterpret_cast<double *>(ws + L.S), *rhs = reinterpret_cast<double *>(ws + L.rhs);
-    double *x = reinterpret_cast<double *>(ws + L.x), *r = reinterpret_cast<double *>(ws + L.r);
-    double *pv = reinterpret_cast<double *>(ws + L.pv), *q = reinterpret_cast<double *>(ws + L.q);
+    Real *S = reinterpret_cast<Real *>(ws + L.S), *rhs = reinterpret_cast<Real *>(ws + L.rhs);
+    Real *x = reinterpret_cast<Real *>(ws + L.x), *r = reinterpret_cast<Real *>(ws + L.r);
+    Real *pv = reinterpret_cast<Real *>(ws + L.pv), *q = reinterpret_cast<Real *>(ws + L.q);
     double *Y = reinterpret_cast<double *>(ws + L.Y), *Yn = reinterpret_cast<double *>(ws + L.Yn);
     double *pn = reinterpret_cast<double *>(ws + L.pn), *an = reinterpret_cast<double *>(ws + L.an);
     double *cs = reinterpret_cast<double *>(ws + L.cs);
@@ -826,7 +835,7 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
         std::swap(P, A);   // level k's rows are the cloud of level k-1
         std::swap(Y, Yn);
     }
-    k_anc_output<<<1, 256, 0, s>>>(M, L.d, Y, x, u0, grad);
+    k_anc_output<Real><<<1, 256, 0, s>>>(M, L.d, Y, x, u0, grad);
     return cudaGetLastError();
 }
 

@@ -580,6 +580,10 @@ def _main(argv=None) -> None:
     ap.add_argument("--time-family", default=None,
                     help="time the launches of one kernel family (e.g. step), or of "
                          "every family (all), with the library's launch profiler")
+    ap.add_argument("--kernel-table", action="store_true",
+                    help="after the timed solves, one more solve under the CUDA activity "
+                         "profiler (torch.profiler): device time per kernel, including the "
+                         "kernels that CUDA graphs launch")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
     x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)) if a.x0 == "uniform"
@@ -588,6 +592,12 @@ def _main(argv=None) -> None:
     solver = Solver(a.kind, a.d, a.N, a.M, a.sigma, a.T, Q=a.Q, precision=a.precision,
                     theta=theta, cg_tol=a.cg_tol, cg_max_iter=a.cg_max_iter, mu0=a.mu0,
                     mu1=a.mu1, sig1=a.sig1)
+    if a.kernel_table:
+        # the activity API is set up before the first solve instantiates its CUDA graphs:
+        # kernels of graphs instantiated earlier may be recorded for one loop iteration only
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]):
+            torch.cuda.synchronize()
     if a.time_products or a.time_family:
         fbsde_profile_start(1 << 20)
         if a.time_family != "all":
@@ -600,6 +610,15 @@ def _main(argv=None) -> None:
         dt = time.perf_counter() - t0
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
               f"u0[0]={float(out['u0'][0]):.12f}")
+    if a.kernel_table:
+        from torch.profiler import ProfilerActivity, profile
+        run = ((lambda: solve_anchored(solver.problem, x0, a.seed)) if a.anchored
+               else (lambda: solver.solve(x0, seed=a.seed)))
+        with profile(activities=[ProfilerActivity.CUDA]) as kp:
+            run()
+            torch.cuda.synchronize()
+        print(kp.key_averages().table(sort_by="cuda_time_total", row_limit=16,
+                                      max_name_column_width=64))
     if a.time_products or a.time_family:
         prof = fbsde_profile_stop()
         for fam in (prof if a.time_family == "all" else [a.time_family or "matvec"]):
