@@ -413,6 +413,19 @@ FBSDE_API const char *fbsde_kernel_name(int family);
 /* Utilities without a counterpart in the paper: a static description of a status code
    (never NULL), and FBSDE_ABI_VERSION of the loaded library. */
 FBSDE_API const char *fbsde_status_string(int status);
+/* Check of the library's bounded device waits (no counterpart in the paper): every wait of
+ * the kernels on an mbarrier gives up after a time limit, records FBSDE_ERR_TIMEOUT in the
+ * solve's status and lets the kernel finish, so that a broken pipeline never hangs the
+ * device.  This launches one warp that waits, with limit_ns, on an mbarrier that nothing
+ * arrives on, and synchronises the stream.
+ *   limit_ns   1 .. 10^9 nanoseconds, else FBSDE_ERR_ARG
+ *   scratch    device, 16 bytes, 8-byte aligned, caller-owned (NULL: FBSDE_ERR_ARG)
+ *   waited_ns  host, may be NULL: the time the wait took
+ * Returns FBSDE_ERR_TIMEOUT when the wait gave up as designed (the expected result),
+ * FBSDE_OK if it did not, FBSDE_ERR_CUDA if the launch or the copy failed. */
+FBSDE_API int fbsde_check_bounded_wait(int64_t limit_ns, void *scratch, int64_t *waited_ns,
+                                       fbsde_stream_t stream);
+
 FBSDE_API int fbsde_abi_version(void);
 
 #ifdef __cplusplus

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fbsde_kernels.cuh"
+#include "fbsde_matvec.cuh"
 
 namespace fbsde {
 namespace {
@@ -37,6 +38,30 @@ bool choose_team(int nch, int &tw, int &vpt, int &teams)
     if (32 * tw > 512) return false;
     teams = std::max(1, 256 / (32 * tw));
     return true;
+}
+
+// Check of the bounded waits: an mbarrier that nothing arrives on, waited on by every
+// thread of one warp with the given limit, twice (the second wait only polls, as after
+// any first timeout).  out[0] = FBSDE_ERR_TIMEOUT when every thread gave up, out[1] = the
+// nanoseconds thread 0 spent.
+static __global__ void __launch_bounds__(32) k_wait_probe(unsigned long long limit_ns, int *out,
+                                                   unsigned long long *ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncwarp();
+    const unsigned long long t0 = dev::globaltimer_ns();
+    bool timed_out = false;
+    dev::mbar_wait_or_flag(&bar, 0u, timed_out, limit_ns);
+    dev::mbar_wait_or_flag(&bar, 0u, timed_out, limit_ns);
+    const bool all = __all_sync(0xffffffffu, timed_out);
+    if (threadIdx.x == 0) {
+        *out = all ? (int)FBSDE_ERR_TIMEOUT : (int)FBSDE_OK;
+        *ns = dev::globaltimer_ns() - t0;
+    }
 }
 
 // check_theta: also require the device theta pointer of the kinds that read it.
@@ -1163,6 +1188,25 @@ const char *fbsde_status_string(int status)
     case FBSDE_ERR_NONFINITE: return "non-finite result";
     }
     return "unknown status";
+}
+
+int fbsde_check_bounded_wait(int64_t limit_ns, void *scratch, int64_t *waited_ns,
+                             fbsde_stream_t stream)
+{
+    if (limit_ns <= 0 || limit_ns > 1000000000LL || !scratch ||
+        (reinterpret_cast<uintptr_t>(scratch) % 8))
+        return FBSDE_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long h[2] = {0, 0};
+    int *out = static_cast<int *>(scratch);
+    unsigned long long *ns = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 8);
+    k_wait_probe<<<1, 32, 0, s>>>((unsigned long long)limit_ns, out, ns);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h, scratch, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    if (waited_ns) *waited_ns = (int64_t)h[1];
+    return (int)(h[0] & 0xffffffffu);
 }
 
 int fbsde_abi_version(void) { return FBSDE_ABI_VERSION; }

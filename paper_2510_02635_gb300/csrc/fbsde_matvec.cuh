@@ -58,25 +58,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 // Waits for the completion of the barrier phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 // Bounded wait whose failure is sticky: after the first timeout of this thread, later
 // waits only poll once, so a broken pipeline costs one kWaitNs per thread, not one per
 // stage.
-__device__ __forceinline__ void mbar_wait_or_flag(uint64_t *bar, uint32_t parity, bool &timed_out)
+__device__ __forceinline__ void mbar_wait_or_flag(uint64_t *bar, uint32_t parity, bool &timed_out,
+                                                  unsigned long long limit_ns = kWaitNs)
 {
     if (timed_out) {
         (void)mbar_try_wait(bar, parity);
         return;
     }
-    if (!mbar_wait(bar, parity)) timed_out = true;
+    if (!mbar_wait(bar, parity, limit_ns)) timed_out = true;
 }
 
 // Bulk copy global -> shared memory; completion is signalled on bar as transaction bytes.

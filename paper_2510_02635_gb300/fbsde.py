@@ -76,7 +76,7 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
            "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch",
-           "fbsde_anchored_diagnostics"]
+           "fbsde_anchored_diagnostics", "fbsde_check_bounded_wait"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 13
 FBSDE_MAX_D = 16384
@@ -133,6 +133,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_solve_batch.restype = C.c_int
         lib.fbsde_anchored_diagnostics.argtypes = [P, V, C.POINTER(fbsde_diag), V]
         lib.fbsde_anchored_diagnostics.restype = C.c_int
+        lib.fbsde_check_bounded_wait.argtypes = [I64, V, C.POINTER(C.c_int64), V]
+        lib.fbsde_check_bounded_wait.restype = C.c_int
         lib.fbsde_adjoint_workspace_bytes.argtypes = [P, I32]
         lib.fbsde_adjoint_workspace_bytes.restype = SZ
         lib.fbsde_adjoint.argtypes = [P, I32, V, U64, U32, V, V, V, V, V, V, SZ, V]
@@ -315,6 +317,15 @@ def fbsde_normals(seed: int, s: int, k: int, j0: int, nj: int, d: int, precision
     return int(load_library().fbsde_normals(int(seed), int(s), int(k), int(j0), int(nj),
                                             int(d), PRECISIONS[precision], _ptr(out),
                                             _stream(stream)))
+
+
+def fbsde_check_bounded_wait(limit_ns: int, scratch, stream=None) -> tuple[int, int]:
+    """(status, waited nanoseconds) of one bounded wait on an mbarrier that nothing
+    arrives on; FBSDE_ERR_TIMEOUT is the expected status."""
+    waited = C.c_int64(0)
+    st = load_library().fbsde_check_bounded_wait(int(limit_ns), _ptr(scratch), C.byref(waited),
+                                                 _stream(stream))
+    return int(st), int(waited.value)
 
 
 def fbsde_status_string(status: int) -> str:

@@ -230,3 +230,12 @@ def test_forward_sde_workspace_and_argument_checks(lib):
     p = _prob(mu0=0.2)
     assert lib.fbsde_adjoint(C.byref(p), 1, fake, 0, 0, fake, fake, None, fake, None, fake,
                              1 << 40, None) == 1
+
+
+def test_bounded_wait_check_argument_errors(lib):
+    """Argument errors of the wait check return before any CUDA call."""
+    fake = C.c_void_p(1 << 20)
+    assert lib.fbsde_check_bounded_wait(0, fake, None, None) == 1
+    assert lib.fbsde_check_bounded_wait(2_000_000_000, fake, None, None) == 1
+    assert lib.fbsde_check_bounded_wait(1000, None, None, None) == 1
+    assert lib.fbsde_check_bounded_wait(1000, C.c_void_p((1 << 20) + 4), None, None) == 1
