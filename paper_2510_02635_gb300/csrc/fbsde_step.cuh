@@ -74,6 +74,17 @@ __device__ __forceinline__ float warp_sum4_scatter(float s0, float s1, float s2,
     return k;
 }
 
+// a * b + c on both halves of a pair at once: the packed FP32 fused multiply-add of this
+// architecture (one instruction for two FMAs)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+// acc + a . b over the four components, as two pairs
+__device__ __forceinline__ float2 dot4x2(float4 a, float4 b, float2 acc)
+{
+    return fma2(hi2(a), hi2(b), fma2(lo2(a), lo2(b), acc));
+}
+
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
 {
     acc = fmaf(a.x, b.x, acc);
@@ -345,18 +356,17 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
         acc[0][v] = acc[1][v] = acc[2][v] = make_float4(0.f, 0.f, 0.f, 0.f);
     // fma of one chunk of a row into the three accumulators of chunk v
     auto acc3 = [&](float4 (&a)[3], const float4 cf, const float4 x) {
-        a[0].x = fmaf(cf.x, x.x, a[0].x);
-        a[0].y = fmaf(cf.x, x.y, a[0].y);
-        a[0].z = fmaf(cf.x, x.z, a[0].z);
-        a[0].w = fmaf(cf.x, x.w, a[0].w);
-        a[1].x = fmaf(cf.y, x.x, a[1].x);
-        a[1].y = fmaf(cf.y, x.y, a[1].y);
-        a[1].z = fmaf(cf.y, x.z, a[1].z);
-        a[1].w = fmaf(cf.y, x.w, a[1].w);
-        a[2].x = fmaf(cf.z, x.x, a[2].x);
-        a[2].y = fmaf(cf.z, x.y, a[2].y);
-        a[2].z = fmaf(cf.z, x.z, a[2].z);
-        a[2].w = fmaf(cf.z, x.w, a[2].w);
+        const float2 xl = lo2(x), xh = hi2(x);
+        const float2 c0 = make_float2(cf.x, cf.x), c1 = make_float2(cf.y, cf.y),
+                     c2 = make_float2(cf.z, cf.z);
+        float2 l = fma2(c0, xl, lo2(a[0])), h = fma2(c0, xh, hi2(a[0]));
+        a[0] = make_float4(l.x, l.y, h.x, h.y);
+        l = fma2(c1, xl, lo2(a[1]));
+        h = fma2(c1, xh, hi2(a[1]));
+        a[1] = make_float4(l.x, l.y, h.x, h.y);
+        l = fma2(c2, xl, lo2(a[2]));
+        h = fma2(c2, xh, hi2(a[2]));
+        a[2] = make_float4(l.x, l.y, h.x, h.y);
     };
     auto p3 = [&](int i) {
         const int b = i & 1;
@@ -426,6 +436,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
         const int tl = tl0;
         const long long j = base + team;
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        float2 q0 = make_float2(0.f, 0.f), q1 = q0, q3 = q0;   // pair sums of the level step
         float4 *dst = reinterpret_cast<float4 *>(ws.row(s, active ? j : base));
         if (terminal) {
             if (active) {
@@ -480,25 +491,27 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Params p)
                             if (i0 + 2 >= d) z.z = 0.0f;
                             if (i0 + 3 >= d) z.w = 0.0f;
                         }
-                        float4 dn;
-                        dn.x = fmaf(wa, dold.x, z.x);
-                        dn.y = fmaf(wa, dold.y, z.y);
-                        dn.z = fmaf(wa, dold.z, z.z);
-                        dn.w = fmaf(wa, dold.w, z.w);
+                        const float2 wa2 = make_float2(wa, wa);
+                        const float2 dl = fma2(wa2, lo2(dold), lo2(z)),
+                                     dh = fma2(wa2, hi2(dold), hi2(z));
+                        const float4 dn = make_float4(dl.x, dl.y, dh.x, dh.y);
                         const float4 ax = reinterpret_cast<const float4 *>(vx)[c];
                         const float4 gg = reinterpret_cast<const float4 *>(vg)[c];
-                        s0 = dot4(ax, dn, s0);
-                        s1 = dot4(dn, dn, s1);
-                        s3 = dot4(gg, dn, s3);
+                        q0 = dot4x2(ax, dn, q0);
+                        q1 = dot4x2(dn, dn, q1);
+                        q3 = dot4x2(gg, dn, q3);
                         if (COSF) {
                             const float4 xc = reinterpret_cast<const float4 *>(vx0)[c];
-                            s2 += (cos_ftz(xc.x + dn.x) + cos_ftz(xc.y + dn.y)) +
-                                  (cos_ftz(xc.z + dn.z) + cos_ftz(xc.w + dn.w));
+                            const float2 xa = __fadd2_rn(lo2(xc), dl), xb = __fadd2_rn(hi2(xc), dh);
+                            s2 += (cos_ftz(xa.x) + cos_ftz(xa.y)) + (cos_ftz(xb.x) + cos_ftz(xb.y));
                         }
                         dst[c] = dn;
                     }
                 }
             }
+            s0 += q0.x + q0.y;
+            s1 += q1.x + q1.y;
+            s3 += q3.x + q3.y;
         }
         if (T >= 32) {   // one partial per warp; lane 8q writes component q
             const float k4 = warp_sum4_scatter(s0, s1, s2, s3, lane);
