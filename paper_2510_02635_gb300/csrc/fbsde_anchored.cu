@@ -20,7 +20,8 @@
 // Kernels: the contractions of FP32 solves with M >= 1024 run on the tensor cores
 // (k_gemm_tc, split TF32, fbsde_tcgemm.cuh), the CG pass's P V^T with the column pass fused
 // into its epilogue; smaller or FP64 solves use the SIMT k_gemm and k_anc_columns.  The
-// per-anchor d-vector kernels (setup, CG pass, Newton) run one warp per anchor.
+// per-anchor d-vector kernels run one warp (setup, Newton) or one block (the CG pass of rows up
+// to 1024 chunks, its vectors in registers) per anchor.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -315,8 +316,7 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc,
                                                               const Real *A, const Real *G2,
                                                               const Real *G3, const double *part,
                                                               Anchor *st, Real *S, Real *rhs,
-                                                              Real *x, Real *r, Real *pv,
-                                                              Real *V)
+                                                              Real *x, Real *r, Real *pv)
 {
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kAncWarps + (threadIdx.x >> 5);
@@ -346,7 +346,6 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_setup(Params p, int nrc,
         x[o + i] = Real(0);
         r[o + i] = b;
         pv[o + i] = b;
-        V[o + i] = b;
         acc[0] += sv * sv;
         acc[1] += b * b;
         acc[2] += sv * b;
@@ -377,8 +376,7 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
                                                            const Real *A, const Real *G,
                                                            const double *part, const Real *S,
                                                            Anchor *st, Real *x, Real *r,
-                                                           Real *pv, Real *q, Real *V,
-                                                           int *active)
+                                                           Real *pv, Real *q, int *active)
 {
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kAncWarps + (threadIdx.x >> 5);
@@ -427,12 +425,160 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_cg(Params p, int nrc, in
     for (int i = lane; i < p.ld; i += 32) {
         const Real pi = r[o + i] + betar * pv[o + i];
         pv[o + i] = pi;
-        V[o + i] = pi;
         b[0] += S[o + i] * pi;
         b[1] += A[o + i] * pi;
     }
     warp_sums(b);
     if (lane == 0) {
+        a.rr = rr_new;
+        a.sp = (double)b[0];
+        a.ap = (double)b[1];
+        a.iters += 1;
+        if (rr_new <= p.cg_tol2 * a.rhs2) {
+            a.done = 1;
+        } else if (a.iters >= p.cg_max_iter) {
+            a.done = 1;
+            a.status = FBSDE_ERR_CG;
+        } else {
+            atomicAdd(active, 1);
+        }
+    }
+}
+
+// Sums of NV values over the nw warps of a block (warp trees, then the warps in order);
+// every thread gets the totals.  sm: this reduction's own [8][NV] slots, so consecutive
+// reductions need no barrier between them.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sums(T (&v)[NV], T (*sm)[NV], int warp, int lane, int nw)
+{
+    warp_sums(v);
+    if (nw == 1) return;
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[warp][i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T s = sm[0][i];
+        for (int w = 1; w < nw; ++w) s += sm[w][i];
+        v[i] = s;
+    }
+}
+
+// The CG pass of k_anc_cg with the anchor's vectors in registers: one block of nw <= 8 warps
+// per anchor, thread t holding the 16-byte chunks t, t + 32 nw, .. (at most C of them).
+// The first phase loads G's splits, A, S, p, r and x together; q stays in registers, and
+// the later phases read only S and A again, so a pass moves each vector about once.
+// Rows of at most 256 C chunks (the host falls back to k_anc_cg beyond that).
+template <typename Real, int C>
+__global__ void __launch_bounds__(256) k_anc_cg_reg(Params p, int nrc, int rows_per_chunk,
+                                                    dev::Band band, int nsplit, const Real *A,
+                                                    const Real *G, const double *part,
+                                                    const Real *S, Anchor *st, Real *x, Real *r,
+                                                    Real *pv, int *active)
+{
+    constexpr int E = Chunk<Real>::E;
+    __shared__ Real red_pq[8][1], red_rn[8][1], red_b[8][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m = blockIdx.x;
+    Anchor &a = st[m];
+    if (a.done) return;   // the whole block
+    double cs[1] = {0.0};   // sum_j T_jm, as in k_anc_cg (every warp the same sum)
+    for (int c = lane; c < nrc; c += 32) {
+        const long long j0 = (long long)c * rows_per_chunk;
+        if (band.hits(j0, min((long long)p.M, j0 + rows_per_chunk), m, m + 1))
+            cs[0] += part[((size_t)c * p.M + m) * 3];
+    }
+    warp_sums(cs);
+    const int nchk = p.ld / E;
+    const size_t o = (size_t)m * p.ld, split = (size_t)p.M * p.ld;
+    const double rr = a.rr;
+    const Real csr = (Real)cs[0], spr = (Real)a.sp, lamr = (Real)a.lam;
+    Chunk<Real> pc[C], qc[C], rc[C], xc[C];
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+        zero(pc[v]);
+        zero(qc[v]);
+        zero(rc[v]);
+        zero(xc[v]);
+    }
+    // G_m: the splits added in z order (split_sum's order), C independent loads per split
+    for (int z = 0; z < nsplit; ++z) {
+#pragma unroll
+        for (int v = 0; v < C; ++v) {
+            const int ci = threadIdx.x + blockDim.x * v;
+            if (ci < nchk) {
+                const Chunk<Real> t = dev::ldg_chunk(G + z * split + o + (size_t)ci * E);
+#pragma unroll
+                for (int e = 0; e < E; ++e) qc[v].v[e] += t.v[e];
+            }
+        }
+    }
+    Real pq[1] = {Real(0)};
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+        const int ci = threadIdx.x + blockDim.x * v;
+        if (ci < nchk) {
+            const size_t ix = o + (size_t)ci * E;
+            const Chunk<Real> ac = dev::ldg_chunk(A + ix), sc = dev::ldg_chunk(S + ix);
+            pc[v] = dev::ld_chunk(pv + ix);
+            rc[v] = dev::ld_chunk(r + ix);
+            xc[v] = dev::ld_chunk(x + ix);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                qc[v].v[e] = qc[v].v[e] - csr * ac.v[e] - sc.v[e] * spr + lamr * pc[v].v[e];
+                pq[0] += pc[v].v[e] * qc[v].v[e];
+            }
+        }
+    }
+    block_sums(pq, red_pq, warp, lane, nw);
+    const double pqd = (double)pq[0];
+    if (!(pqd > 0.0) || !isfinite(pqd)) {   // the same value in every thread
+        if (threadIdx.x == 0) {
+            a.done = 1;
+            if (!(rr <= p.cg_tol2 * a.rhs2)) a.status = FBSDE_ERR_CG;
+        }
+        return;
+    }
+    const double step = rr / pqd;
+    const Real stepr = (Real)step;
+    Real rn[1] = {Real(0)};
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+        const int ci = threadIdx.x + blockDim.x * v;
+        if (ci < nchk) {
+            const size_t ix = o + (size_t)ci * E;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                xc[v].v[e] += stepr * pc[v].v[e];
+                rc[v].v[e] = rc[v].v[e] - stepr * qc[v].v[e];
+                rn[0] += rc[v].v[e] * rc[v].v[e];
+            }
+            dev::st_chunk(x + ix, xc[v]);
+            dev::st_chunk(r + ix, rc[v]);
+        }
+    }
+    block_sums(rn, red_rn, warp, lane, nw);
+    const double rr_new = (double)rn[0], beta = rr_new / rr;
+    const Real betar = (Real)beta;
+    Real b[2] = {Real(0), Real(0)};
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+        const int ci = threadIdx.x + blockDim.x * v;
+        if (ci < nchk) {
+            const size_t ix = o + (size_t)ci * E;
+            const Chunk<Real> ac = dev::ldg_chunk(A + ix), sc = dev::ldg_chunk(S + ix);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                pc[v].v[e] = rc[v].v[e] + betar * pc[v].v[e];
+                b[0] += sc.v[e] * pc[v].v[e];
+                b[1] += ac.v[e] * pc[v].v[e];
+            }
+            dev::st_chunk(pv + ix, pc[v]);
+        }
+    }
+    block_sums(b, red_b, warp, lane, nw);
+    if (threadIdx.x == 0) {
         a.rr = rr_new;
         a.sp = (double)b[0];
         a.ap = (double)b[1];
@@ -520,7 +666,7 @@ struct Lay {
     size_t rs;   // bytes of one stream-precision value
     int nrc, nsplit, kc;   // row chunks of the column pass; K splits (kc rows each) of the
                            // tall contractions
-    size_t P, A, YP, V, G1, W, T, G2, G3, S, rhs, x, r, pv, q, Y, Yn, pn, an, cs, st, cnt, total;
+    size_t P, A, YP, G1, W, T, G2, G3, S, rhs, x, r, pv, q, Y, Yn, pn, an, cs, st, cnt, total;
 };
 
 bool lay(const fbsde_problem *P, Lay &L)
@@ -552,7 +698,6 @@ bool lay(const fbsde_problem *P, Lay &L)
     L.P = take(M * ld * L.rs);
     L.A = take(M * ld * L.rs);
     L.YP = take(M * ld * L.rs);
-    L.V = take(M * ld * L.rs);
     L.G1 = take(M * M * L.rs);
     L.W = take(M * M * L.rs);
     L.T = take(M * M * L.rs);
@@ -726,6 +871,20 @@ __global__ void k_anc_loop_next(int *cnt, int max_iter, cudaGraphConditionalHand
 // then the levels k = N-1..0, each level's CG passes as a conditional while node whose
 // body is captured on the stream b.  The device status accumulates in cnt[1].
 // Kb: particles per anchor's regression (the cyclic window; Kb = M: all of them).
+// Block of the register-resident CG pass for rows of nchk 16-byte chunks: nw warps and C
+// chunks per thread with 32 nw C >= nchk, C in {1, 2, 4} and nw <= 8 (C = 0: rows longer
+// than 1024 chunks, which take the streaming k_anc_cg).
+struct CgShape {
+    int nw, C;
+};
+CgShape cg_shape(int nchk)
+{
+    if (nchk > 32 * 8 * 4) return {0, 0};
+    const int nw = std::min(8, (nchk + 127) / 128);
+    const int per = (nchk + 32 * nw - 1) / (32 * nw);
+    return {nw, per <= 1 ? 1 : per <= 2 ? 2 : 4};
+}
+
 template <typename Real>
 cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
                      uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
@@ -735,7 +894,7 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
     Params p = params_of(Pb, L, seed);
     const int M = (int)L.M, ld = L.ld;
     Real *P = reinterpret_cast<Real *>(ws + L.P), *A = reinterpret_cast<Real *>(ws + L.A);
-    Real *YP = reinterpret_cast<Real *>(ws + L.YP), *V = reinterpret_cast<Real *>(ws + L.V);
+    Real *YP = reinterpret_cast<Real *>(ws + L.YP);
     Real *G1 = reinterpret_cast<Real *>(ws + L.G1), *W = reinterpret_cast<Real *>(ws + L.W);
     Real *T = reinterpret_cast<Real *>(ws + L.T);
     Real *G2 = reinterpret_cast<Real *>(ws + L.G2), *G3 = reinterpret_cast<Real *>(ws + L.G3);
@@ -759,6 +918,7 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
     // K-splits off it are skipped); T's entries off the band stay zero for the whole solve
     const dev::Band band{(long long)M, Kb < M ? Kb : (long long)M};
     if (fused && Kb < M) ANC_TRY(cudaMemsetAsync(T, 0, (size_t)M * M * sizeof(Real), s));
+    const CgShape cg = cg_shape(ld / Chunk<Real>::E);
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
         const double a = (double)k / (double)(k + 1), bb = p.sigma * std::sqrt(p.dt * a);
@@ -773,7 +933,7 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
         ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, P, ld, G2, ld, cnt + 1, s, band)));    // W^T P
         ANC_TRY((gemm<Real, true>(M, ld, M, L.kc, W, M, YP, ld, G3, ld, cnt + 1, s, band)));   // W^T (Y P)
         k_anc_setup<Real><<<awarps, 32 * kAncWarps, 0, s>>>(p, L.nrc, L.nsplit, A, G2, G3, cs, st, S,
-                                                           rhs, x, r, pv, V);
+                                                           rhs, x, r, pv);
         ANC_TRY(cudaGetLastError());
         // the CG passes: a conditional while node (body on b) that repeats while some anchor
         // iterates on and fewer than cg_max_iter passes ran
@@ -804,10 +964,10 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
             cudaError_t eb = cudaSuccess;
             if (fused) {   // T and its column sums straight from the product's epilogue
                 if constexpr (sizeof(Real) == 4)
-                    eb = gemm_tc<false>(M, M, ld, ld, P, ld, V, ld, TcColumnsEpi{W, T, st, cs, M},
+                    eb = gemm_tc<false>(M, M, ld, ld, P, ld, pv, ld, TcColumnsEpi{W, T, st, cs, M},
                                         cnt + 1, b, band);
             } else {
-                eb = gemm<Real, false>(M, M, ld, ld, P, ld, V, ld, G1, M, cnt + 1, b, band);   // U = P V^T
+                eb = gemm<Real, false>(M, M, ld, ld, P, ld, pv, ld, G1, M, cnt + 1, b, band);   // U = P V^T
                 if (eb == cudaSuccess) {
                     k_anc_columns<Real><<<cgrid, 128, 0, b>>>(p, 1, 0.0, Kb, G1, pn, an, Y, W, T, st, cs);
                     eb = cudaGetLastError();
@@ -816,9 +976,26 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
             if (eb == cudaSuccess)
                 eb = gemm<Real, true>(M, ld, M, L.kc, T, M, P, ld, G2, ld, cnt + 1, b, band);   // T^T P
             if (eb == cudaSuccess) {
-                k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, b>>>(
-                    p, fused ? nrc_fused : L.nrc, fused ? dev::kTcBM : kRowChunk, band, L.nsplit, A,
-                    G2, cs, S, st, x, r, pv, q, V, cnt);
+                const int nrc_cg = fused ? nrc_fused : L.nrc;
+                const int rpc = fused ? dev::kTcBM : kRowChunk;
+                switch (cg.C) {
+                case 1:
+                    k_anc_cg_reg<Real, 1><<<M, 32 * cg.nw, 0, b>>>(p, nrc_cg, rpc, band, L.nsplit,
+                                                                   A, G2, cs, S, st, x, r, pv, cnt);
+                    break;
+                case 2:
+                    k_anc_cg_reg<Real, 2><<<M, 32 * cg.nw, 0, b>>>(p, nrc_cg, rpc, band, L.nsplit,
+                                                                   A, G2, cs, S, st, x, r, pv, cnt);
+                    break;
+                case 4:
+                    k_anc_cg_reg<Real, 4><<<M, 32 * cg.nw, 0, b>>>(p, nrc_cg, rpc, band, L.nsplit,
+                                                                   A, G2, cs, S, st, x, r, pv, cnt);
+                    break;
+                default:
+                    k_anc_cg<Real><<<awarps, 32 * kAncWarps, 0, b>>>(p, nrc_cg, rpc, band, L.nsplit,
+                                                                     A, G2, cs, S, st, x, r, pv, q,
+                                                                     cnt);
+                }
                 eb = cudaGetLastError();
             }
             if (eb == cudaSuccess) {
