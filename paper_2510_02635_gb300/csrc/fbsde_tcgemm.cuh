@@ -15,9 +15,9 @@
 // k per pipeline stage, two stages, 256 threads.  All threads load the stage after next
 // into registers and split the next one into shared memory while the tensor core runs the
 // current one; one thread issues the MMAs and commits them to the stage's mbarrier, whose
-// completion frees the stage.  Two or three
-// blocks are resident per SM (64 KB of shared memory and 128 tensor-memory columns each;
-// the launch bounds keep registers for two), so one block's loads overlap another's MMAs.
+// completion frees the stage.  Three blocks
+// are resident per SM (64 KB of shared memory and 128 tensor-memory columns each; the
+// launch bounds hold a thread to 80 registers), so one block's loads overlap another's MMAs.
 // Shared memory caps an SM at three blocks, 384 of its 512 tensor-memory columns, so the
 // allocation never waits for another block to free columns.
 //
@@ -109,51 +109,84 @@ __device__ __forceinline__ void tf32_split(float a, float &hi, float &lo)
     lo = a - hi;
 }
 
-// Raw values of one operand tile for k in [k0, k0 + 16): two 4-wide k chunks of one row
-// per thread.  Row r of the tile is tile row (idx & 127), chunk idx >> 7.
-//   TN = false: X(row, k) = X[row * ldx + k] (k contiguous; ldx, k0 and ke multiples of 4,
-//               X 16-byte aligned: one 16-byte load per chunk);
-//   TN = true:  X(row, k) = X[k * ldx + row] (rows contiguous: four coalesced loads).
-// Rows >= nrows and k >= ke read as 0.
-template <bool TN>
-__device__ __forceinline__ void tc_load(float4 (&v)[2], const float *__restrict__ X, int ldx,
-                                        int row0, int nrows, int k0, int ke)
-{
+// Loader of one operand: each stage, a thread loads two items (tile row, 4-wide k chunk)
+// of the 128-row x 16-k tile into registers, stages in increasing k order.
+//   TN = false: X(row, k) = X[row * ldx + k] (k contiguous; ldx, kb and ke multiples of 4,
+//               X 16-byte aligned: one 16-byte load per item).  Warp w, lane l, item u:
+//               row 8 (w + 8 u) + (l & 7), chunk l >> 3, so a warp reads 8 rows x 64
+//               contiguous bytes (whole sectors) and each 8-lane phase of its 16-byte
+//               shared-memory stores writes 8 rows of one chunk (128 contiguous bytes).
+//   TN = true:  X(row, k) = X[k * ldx + row] (rows contiguous).  Item idx = threadIdx.x +
+//               256 u: row idx & 127, chunk idx >> 7, so a warp reads 32 consecutive rows of
+//               one k per load.
+// Rows >= nrows and k >= ke read as 0.  The item addresses are set up once and advanced by
+// one stage per load; only a stage that ends past ke checks its values one by one.
+template <bool TN> struct TcLoader {
+    const float *p[2];   // the item's first value at the next stage's k
+    uint32_t soff[2];    // the item's byte offset in an operand part
+    int kq[2];           // k offset of the item within a stage (4 chunk)
+    bool ok[2];          // row < nrows
+    int k0, ldx;         // k of the next stage; leading dimension
+    __device__ __forceinline__ TcLoader(const float *__restrict__ X, int ldx_, int row0,
+                                        int nrows, int kb)
+        : k0(kb), ldx(ldx_)
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int idx = threadIdx.x + kTcThreads * u;
-        const int gr = row0 + (idx & (kTcBM - 1)), gk = k0 + 4 * (idx >> 7);
-        float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (gr < nrows) {
+        for (int u = 0; u < 2; ++u) {
+            int row, chunk;
             if (TN) {
-                const float *p = X + (size_t)gk * ldx + gr;
-                if (gk < ke) t.x = __ldg(p);
-                if (gk + 1 < ke) t.y = __ldg(p + ldx);
-                if (gk + 2 < ke) t.z = __ldg(p + 2 * (size_t)ldx);
-                if (gk + 3 < ke) t.w = __ldg(p + 3 * (size_t)ldx);
-            } else if (gk < ke) {
-                t = __ldg(reinterpret_cast<const float4 *>(X + (size_t)gr * ldx + gk));
+                const int idx = threadIdx.x + kTcThreads * u;
+                row = idx & (kTcBM - 1);
+                chunk = idx >> 7;
+            } else {
+                row = 8 * (warp + 8 * u) + (lane & 7);
+                chunk = lane >> 3;
             }
+            kq[u] = 4 * chunk;
+            soff[u] = (uint32_t)chunk * kTcChunkBytes + (uint32_t)row * 16u;
+            ok[u] = row0 + row < nrows;
+            p[u] = TN ? X + (size_t)(kb + kq[u]) * ldx + (row0 + row)
+                      : X + (size_t)(row0 + row) * ldx + (kb + kq[u]);
         }
-        v[u] = t;
     }
-}
-
-__device__ __forceinline__ void tc_store(const float4 (&v)[2], uint8_t *hi, uint8_t *lo)
-{
+    __device__ __forceinline__ void load(float4 (&v)[2], int ke)
+    {
+        const bool full = k0 + kTcBK <= ke;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int idx = threadIdx.x + kTcThreads * u;
-        const uint32_t off = (uint32_t)(idx >> 7) * kTcChunkBytes + (uint32_t)(idx & (kTcBM - 1)) * 16u;
-        float4 h, l;
-        tf32_split(v[u].x, h.x, l.x);
-        tf32_split(v[u].y, h.y, l.y);
-        tf32_split(v[u].z, h.z, l.z);
-        tf32_split(v[u].w, h.w, l.w);
-        *reinterpret_cast<float4 *>(hi + off) = h;
-        *reinterpret_cast<float4 *>(lo + off) = l;
+        for (int u = 0; u < 2; ++u) {
+            float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const int gk = k0 + kq[u];
+            if (ok[u]) {
+                if (TN) {
+                    if (full || gk < ke) t.x = __ldg(p[u]);
+                    if (full || gk + 1 < ke) t.y = __ldg(p[u] + ldx);
+                    if (full || gk + 2 < ke) t.z = __ldg(p[u] + 2 * (size_t)ldx);
+                    if (full || gk + 3 < ke) t.w = __ldg(p[u] + 3 * (size_t)ldx);
+                } else if (full || gk < ke) {
+                    t = __ldg(reinterpret_cast<const float4 *>(p[u]));
+                }
+            }
+            v[u] = t;
+            p[u] += TN ? (size_t)kTcBK * ldx : (size_t)kTcBK;
+        }
+        k0 += kTcBK;
     }
-}
+    // Split the two items into the hi and lo parts of an operand stage.
+    __device__ __forceinline__ void store(const float4 (&v)[2], uint8_t *hi, uint8_t *lo) const
+    {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float4 h, l;
+            tf32_split(v[u].x, h.x, l.x);
+            tf32_split(v[u].y, h.y, l.y);
+            tf32_split(v[u].z, h.z, l.z);
+            tf32_split(v[u].w, h.w, l.w);
+            *reinterpret_cast<float4 *>(hi + soff[u]) = h;
+            *reinterpret_cast<float4 *>(lo + soff[u]) = l;
+        }
+    }
+};
 
 // Band of the batch reading (Remark 2.1): anchor m's regression uses the particles
 // j = (m + q) mod M, q < Kb, so only entries (j, m) with (j - m) mod M < Kb are ever used.
@@ -206,7 +239,7 @@ struct TcStore {
 // TN products (rows m, contraction over j) treat a split whose rows j miss the band of the
 // tile's anchors as empty, so the epilogue writes its zero partial.
 template <bool TN, class Epi>
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 3)
     k_gemm_tc(int Mr, int Nc, int K, int kc, const float *__restrict__ A, int lda,
               const float *__restrict__ B, int ldb, Epi epi, int *status, Band band)
 {
@@ -241,27 +274,27 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     // Raw values of the next two stages in registers (even and odd steps): a stage's loads
     // are issued two steps before it is stored, so their latency spans two steps.
     float4 va0[2], vb0[2], va1[2], vb1[2];
+    TcLoader<TN> la(A, lda, r0, Mr, kb), lb(B, ldb, c0, Nc, kb);
     if (nk > 0) {
-        tc_load<TN>(va0, A, lda, r0, Mr, kb, ke);
-        tc_load<TN>(vb0, B, ldb, c0, Nc, kb, ke);
+        la.load(va0, ke);
+        lb.load(vb0, ke);
     }
     if (nk > 1) {
-        tc_load<TN>(va1, A, lda, r0, Mr, kb + kTcBK, ke);
-        tc_load<TN>(vb1, B, ldb, c0, Nc, kb + kTcBK, ke);
+        la.load(va1, ke);
+        lb.load(vb1, ke);
     }
     auto step = [&](int t, float4 (&va)[2], float4 (&vb)[2]) {
         const int b = t & 1;
         uint8_t *stg = tsm + b * kTcStageBytes;
         // the stage's previous MMAs (step t - 2) must be done before it is overwritten
         if (t >= 2) mbar_wait_or_flag(&bar[b], (uint32_t)((t - 2) >> 1) & 1u, timed_out);
-        tc_store(va, stg, stg + kTcPartBytes);
-        tc_store(vb, stg + 2 * kTcPartBytes, stg + 3 * kTcPartBytes);
+        la.store(va, stg, stg + kTcPartBytes);
+        lb.store(vb, stg + 2 * kTcPartBytes, stg + 3 * kTcPartBytes);
         fence_async_smem();
         __syncthreads();
         if (t + 2 < nk) {   // loads of step t + 2 overlap this step's MMAs and the next step
-            const int k0 = kb + (t + 2) * kTcBK;
-            tc_load<TN>(va, A, lda, r0, Mr, k0, ke);
-            tc_load<TN>(vb, B, ldb, c0, Nc, k0, ke);
+            la.load(va, ke);
+            lb.load(vb, ke);
         }
         if (threadIdx.x == 0) {
             tc_fence_after();
