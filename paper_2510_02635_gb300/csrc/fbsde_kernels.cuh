@@ -1216,6 +1216,24 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(Params p, int 
     }
 }
 
+// Four consecutive values at a 16-byte aligned address (two 16-byte accesses for doubles,
+// one for floats).
+__device__ __forceinline__ void ld4(double (&v)[4], const double *q)
+{
+    const double2 a = *reinterpret_cast<const double2 *>(q);
+    const double2 b = *reinterpret_cast<const double2 *>(q + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(double *q, const double (&v)[4])
+{
+    *reinterpret_cast<double2 *>(q) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(q + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(float *q, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 // One pass of the CG iteration of Chronopoulos and Gear (1989), the form of conjugate
 // gradients with a single reduction phase per iteration.  The product w = A r and the
 // scalars beta, a of the pass come from k_reduce_partials; here
@@ -1247,21 +1265,37 @@ __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditional
         const int i0 = blockIdx.x * kRedTile + 4 * lane;
         double sr = 0.0, rr = 0.0;
         if (ok && i0 < p.ld) {  // ld is a multiple of 4
+            // every value of the lane's four elements is loaded before the first store
+            // (the vectors may alias as far as the compiler can tell, so it would not
+            // move a later element's loads above an earlier element's stores)
+            double rv[4], wv[4], pv[4], svv[4], xv[4], Sv[4];
+            ld4(rv, r + i0);
+            ld4(wv, w + i0);
+            ld4(xv, x + i0);
+            ld4(Sv, S + i0);
+            if (t > 0) {
+                ld4(pv, pp + i0);
+                ld4(svv, sv + i0);
+            }
+            Real rn4[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int i = i0 + e;
-                const double ri = r[i], wi = w[i];
-                const double pi = t > 0 ? ri + beta * pp[i] : ri;
-                const double si = t > 0 ? wi + beta * sv[i] : wi;
-                pp[i] = pi;
-                sv[i] = si;
-                x[i] += a * pi;
-                const double rn = ri - a * si;
-                r[i] = rn;
-                rR[i] = (Real)rn;
-                sr += S[i] * rn;
+                const double pi = t > 0 ? rv[e] + beta * pv[e] : rv[e];
+                const double si = t > 0 ? wv[e] + beta * svv[e] : wv[e];
+                pv[e] = pi;
+                svv[e] = si;
+                xv[e] += a * pi;
+                const double rn = rv[e] - a * si;
+                rv[e] = rn;
+                rn4[e] = (Real)rn;
+                sr += Sv[e] * rn;
                 rr += rn * rn;
             }
+            st4(pp + i0, pv);
+            st4(sv + i0, svv);
+            st4(x + i0, xv);
+            st4(r + i0, rv);
+            st4(rR + i0, rn4);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {

@@ -103,6 +103,30 @@ def test_uniform_weights_equal_the_single_anchor_solve(prec, tol):
     assert torch.all(torch.linalg.norm(a["grad"] - g, dim=1) <= tol * scale)
 
 
+@pytest.mark.parametrize("prec,tol,d", [("fp32", TOL_FP32, 4096), ("fp32", TOL_FP32, 4100),
+                                        ("fp64", TOL_FP64, 2048), ("fp64", TOL_FP64, 2052)])
+def test_uniform_weights_on_both_sides_of_the_register_row_limit(prec, tol, d):
+    """Rows of 1024 16-byte chunks (FP32 d = 4096, FP64 d = 2048) are the longest whose CG
+    pass keeps the anchor's vectors in registers (eight warps of four chunks per thread);
+    one chunk more takes the streaming warp-per-anchor pass.  Both equal the single-anchor
+    solve under uniform weights.  M < d, so the ridge is the mean eigenvalue."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    M, N, Q = 180, 3, 2
+    x0 = torch.tensor(np.random.default_rng(d).normal(scale=0.02, size=(Q, d)), device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, prec, h=math.inf, ridge_rel=1.0,
+                        cg_tol=1e-13 if prec == "fp64" else 1e-7, cg_max_iter=1000)
+    a = fb.solve_anchored(p, x0, 5, 0)
+    ws = torch.empty(fb.fbsde_workspace_bytes(p, Q), dtype=torch.uint8, device="cuda")
+    u = torch.empty(Q, dtype=torch.float64, device="cuda")
+    g = torch.empty(Q, d, dtype=torch.float64, device="cuda")
+    fb.check(fb.fbsde_solve(p, Q, x0, 5, 0, u, g, ws))
+    torch.cuda.synchronize()
+    assert a["status"] == 0
+    assert torch.all(torch.abs(a["u0"] - u) <= tol * torch.abs(u))
+    scale = torch.maximum(torch.linalg.norm(g, dim=1), torch.abs(u))
+    assert torch.all(torch.linalg.norm(a["grad"] - g, dim=1) <= tol * scale)
+
+
 def test_argument_errors():
     from paper_2510_02635_gb300 import fbsde as fb
     fb.load_library()
