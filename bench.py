@@ -487,12 +487,27 @@ def extra_anchored() -> dict:
                    "cg_passes_per_level": dgb.cg_iters_total / w.N}
             if st_b[0] == 0:
                 rec.update(u0=u_b, abs_err=abs(u_b - exact))
+
+            # the same regressions solved directly (L D L^T of each anchor's operator)
+            def run_direct():
+                fbsde.check(fbsde.fbsde_solve_batch_direct(pb, K, 1, x0, w.seed, 0, u, g, wsb))
+
+            ms_d = _events_ms(run_direct, 3)
+            st_d = int(fbsde.fbsde_anchored_diagnostics(pb, wsb).status)
+            rec["direct"] = {"ms_per_solve": ms_d, "status": st_d}
+            if st_d == 0:
+                u_d = float(u[0])
+                rec["direct"].update(u0=u_d, abs_err=abs(u_d - exact))
+                if st_b[0] == 0:
+                    rec["direct"]["rel_diff_u0_vs_cg"] = abs(u_d - u_b) / abs(u_b)
             out["batch"].append(rec)
             del wsb
         except Exception as e:   # reported in the line, never fatal to the bench
             out["batch"].append({"K": K, "M": Mb, "error": repr(e)})
     if out["batch"] and "ms_per_solve" in out["batch"][0]:
         out["batch_speedup_vs_all_particles"] = ms / out["batch"][0]["ms_per_solve"]
+        out["batch_direct_speedup_vs_all_particles"] = (
+            ms / out["batch"][0]["direct"]["ms_per_solve"])
     return out
 
 

@@ -45,7 +45,7 @@ extern "C" {
 
 typedef struct CUstream_st *fbsde_stream_t; /* the same handle as cudaStream_t */
 
-#define FBSDE_ABI_VERSION 2
+#define FBSDE_ABI_VERSION 3
 #define FBSDE_MAX_D 16384 /* largest dimension d accepted */
 #define FBSDE_MAX_D_FP64 10240 /* largest d of the FP64 path (one team of at most 10 warps
                                   of 16 chunks per thread per row in the product kernel) */
@@ -271,6 +271,27 @@ FBSDE_API int fbsde_anchored_diagnostics(const fbsde_problem *P, const void *wor
 FBSDE_API int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
                                 uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
                                 void *workspace, size_t workspace_bytes, fbsde_stream_t stream);
+
+/* The batch reading of fbsde_solve_batch with each anchor's regression solved directly
+ * instead of by CG passes, so that its cost no longer grows with the CG's pass count: per
+ * level and anchor, one block forms the weighted second moment of the anchor's window of
+ * K particles (sum over the window of w D D^T, D = X_{k+1}^j - X_k^m), the CG form's
+ * operator Gamma_m + lambda_m I from it (the same S_m, lambda_m and right-hand side),
+ * factorises it as L D L^T and solves with the two triangular factors, all in the stream
+ * precision.  Rows as in fbsde_solve_batch; the result is the same regression up to
+ * rounding (the CG stops at cg_tol, this solve is exact up to its rounding).
+ *   1 <= d <= FBSDE_BATCH_DIRECT_MAX_D and ridge_rel > 0 (the ridge keeps every pivot of
+ *   the factorisation at least lambda_m), else FBSDE_ERR_ARG.  K, Q, the buffers, the
+ *   workspace (fbsde_anchored_workspace_bytes), the asynchronous launch and the return codes
+ *   are those of fbsde_solve_batch.  A pivot that rounding still leaves not positive and
+ *   finite leaves that anchor's slope at 0 and sets the device status FBSDE_ERR_CG;
+ *   fbsde_anchored_diagnostics reads it and counts no CG passes.
+ */
+#define FBSDE_BATCH_DIRECT_MAX_D 128
+FBSDE_API int fbsde_solve_batch_direct(const fbsde_problem *P, int64_t K, int32_t Q,
+                                       const double *x0, uint64_t seed, uint32_t solve_index0,
+                                       double *u0, double *grad_u0, void *workspace,
+                                       size_t workspace_bytes, fbsde_stream_t stream);
 
 /* Bytes of device workspace that fbsde_adjoint needs (the solve's workspace plus a tape
    of N (M + 2 d) values per query).  0 when the arguments are invalid. */

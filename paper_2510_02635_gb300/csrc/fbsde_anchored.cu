@@ -594,6 +594,248 @@ __global__ void __launch_bounds__(256) k_anc_cg_reg(Params p, int nrc, int rows_
     }
 }
 
+// Direct solve of each anchor's regression over its batch (the batch reading of Remark
+// 2.1), in place of the CG passes: one block per anchor m, of one thread per tile with
+// TPT = 1 (rounded up to whole warps), of kDirThreads threads with TPT = 2.
+//   1. The weighted second moment of the window, sum_q w_jm D_j D_j^T with D_j = P_j - A_m
+//      over j = (m + q) mod M, q < Kb, summed over q in order in the stream precision: the
+//      lower triangle in 8 x 4 tiles (rows 8 I.., columns 4 K.., 4 K <= 8 I + 7), at most
+//      TPT tiles in registers per thread (TPT = 1 while the triangle has at most
+//      kDirThreads tiles, d <= 120); the window's rows pass through shared
+//      memory kDirRows at a time (one warp per row), padded with zeros to a multiple of 8.
+//   2. Gamma_m + lambda_m I = moment / W_m - S_m S_m^T + lambda_m I, the operator of the
+//      CG pass (Eq. 3.19's), in the same registers.
+//   3. Its LDL^T factorisation, right-looking on the registers with one barrier per column
+//      (the column passes through shared memory, where it stays as the factor; the
+//      operator is symmetric positive definite for lambda_m > 0, so no pivoting), then
+//      L y = rhs, D z = y, L^T x = z by one warp with the vector in registers.
+// The entry point requires ridge_rel > 0, so every pivot is at least lambda_m in exact
+// arithmetic; a pivot that is still not positive and finite leaves x = 0 and the anchor's
+// status FBSDE_ERR_CG.  Anchors whose right-hand side is zero (done after the setup) keep
+// x = 0.
+constexpr int kDirThreads = 256, kDirRows = 32, kDirMaxD = 128;
+// Padded length of a row (and pitch of the factor's columns): a multiple of 8.
+__host__ __device__ inline int dir_pad(int d) { return (d + 7) / 8 * 8; }
+inline size_t dir_smem_bytes(int d, size_t rs)
+{
+    const size_t dp = (size_t)dir_pad(d);
+    const size_t fac = (size_t)d * dp + dp;    // the factor's columns, S_m
+    const size_t rows = 2 * (size_t)kDirRows * dp;   // w D and D of the rows
+    return std::max(fac, rows) * rs;
+}
+template <typename Real> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void ld(float (&v)[4], const float *q)
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(q);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void ld(double (&v)[4], const double *q)
+    {
+        const double2 a = *reinterpret_cast<const double2 *>(q);
+        const double2 b = *reinterpret_cast<const double2 *>(q + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <typename Real, int TPT>
+__global__ void __launch_bounds__(kDirThreads) k_anc_direct(Params p, long long Kb,
+                                                             const Real *P, const Real *A,
+                                                             const Real *W, const Real *S,
+                                                             const Real *rhs, Anchor *st,
+                                                             Real *x)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Real *G = reinterpret_cast<Real *>(dsm);
+    const int m = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int d = p.d, ld = p.ld, dp = dir_pad(d);
+    Anchor &a = st[m];
+    if (a.done) return;   // the whole block
+    const size_t o = (size_t)m * ld;
+    const int nI = dp / 8, nK = dp / 4;
+    // the thread's tiles, tile b counted along the rows of tiles: row I holds
+    // min(2 I + 2, nK) tiles
+    int ti[TPT], tk[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+        int b = t + (int)blockDim.x * u;
+        ti[u] = -1;
+        tk[u] = 0;
+        for (int I = 0; I < nI; ++I) {
+            const int n = min(2 * I + 2, nK);
+            if (b < n) {
+                ti[u] = I;
+                tk[u] = b;
+                break;
+            }
+            b -= n;
+        }
+    }
+    Real acc[TPT][8][4];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) acc[u][ii][kk] = Real(0);
+    Real *Dw = G, *Dr = G + (size_t)kDirRows * dp;   // the rows: w D and D
+    for (long long q0 = 0; q0 < Kb; q0 += kDirRows) {
+        const int nr = (int)min((long long)kDirRows, Kb - q0);
+        __syncthreads();   // the previous rows are used up
+        for (int r = warp; r < nr; r += (int)(blockDim.x >> 5)) {
+            long long j = m + q0 + r;
+            if (j >= p.M) j -= p.M;
+            const Real w = W[(size_t)j * p.M + m];
+            const Real *pj = P + (size_t)j * ld;
+            for (int i = lane; i < dp; i += 32) {
+                const Real dv = i < d ? pj[i] - A[o + i] : Real(0);
+                Dr[r * dp + i] = dv;
+                Dw[r * dp + i] = w * dv;
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) {
+#pragma unroll
+            for (int u = 0; u < TPT; ++u) {
+                if (ti[u] < 0) continue;
+                Real wi[8], dk[4];
+                Vec4<Real>::ld(*reinterpret_cast<Real(*)[4]>(wi), Dw + r * dp + 8 * ti[u]);
+                Vec4<Real>::ld(*reinterpret_cast<Real(*)[4]>(wi + 4), Dw + r * dp + 8 * ti[u] + 4);
+                Vec4<Real>::ld(dk, Dr + r * dp + 4 * tk[u]);
+#pragma unroll
+                for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) acc[u][ii][kk] += wi[ii] * dk[kk];
+            }
+        }
+    }
+    __syncthreads();   // the row buffers become the factor's columns
+    Real *Lc = G;                          // column c of the factor at Lc[c * dp + i], i >= c
+    Real *Sv = G + (size_t)d * dp;         // S_m
+    for (int e = t; e < d * dp; e += blockDim.x) Lc[e] = Real(0);   // padding stays 0
+    for (int i = t; i < d; i += blockDim.x) Sv[i] = S[o + i];
+    __syncthreads();
+    // Gamma + lambda I in the same registers: entry (8 I + ii, 4 K + kk) of tile u
+    const Real invW = (Real)(1.0 / a.W), lam = (Real)a.lam;
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+        if (ti[u] < 0) continue;
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int i = 8 * ti[u] + ii, k = 4 * tk[u] + kk;
+                Real g = Real(0);
+                if (i < d && k <= i) {
+                    g = acc[u][ii][kk] * invW - Sv[i] * Sv[k];
+                    if (i == k) g += lam;
+                }
+                acc[u][ii][kk] = g;
+            }
+    }
+    // LDL^T, right-looking on the registers: before step c the owners of column c (entries
+    // (i, c), c <= i < d, every update of the steps before applied) write it to Lc; after
+    // the barrier every thread updates its entries (i, k), c < k <= i, by
+    // -= Lc[c][i] Lc[c][k] / D_c with D_c = Lc[c][c].  The column's entries above c and
+    // beyond d are zero in Lc, so tiles wholly below and right of c need no masks; the
+    // entries above the diagonal of a tile that crosses it are never read.
+    bool fail = false;
+    for (int c = 0; c < d; ++c) {
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            if (ti[u] < 0 || tk[u] != (c >> 2)) continue;
+#pragma unroll
+            for (int ii = 0; ii < 8; ++ii) {
+                const int i = 8 * ti[u] + ii;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    if ((c & 3) == kk && i >= c && i < d) Lc[c * dp + i] = acc[u][ii][kk];
+            }
+        }
+        __syncthreads();
+        const Real piv = Lc[c * dp + c];   // the same value in every thread
+        if (!(piv > Real(0)) || !isfinite(piv)) {
+            fail = true;
+            break;
+        }
+        const Real ip = Real(1) / piv;
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            if (ti[u] < 0 || 4 * tk[u] + 3 <= c) continue;   // every column of the tile done
+            Real li[8], lk[4];
+            Vec4<Real>::ld(*reinterpret_cast<Real(*)[4]>(li), Lc + c * dp + 8 * ti[u]);
+            Vec4<Real>::ld(*reinterpret_cast<Real(*)[4]>(li + 4), Lc + c * dp + 8 * ti[u] + 4);
+            Vec4<Real>::ld(lk, Lc + c * dp + 4 * tk[u]);
+            if (4 * tk[u] <= c) {   // the tile holds column c: only its columns k > c move
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    if (4 * tk[u] + kk <= c) lk[kk] = Real(0);
+            }
+            // rows i <= c hold entries above the diagonal or finished ones: the column's
+            // entry there is Lc[c][i], zero above c and D_c at c
+            if (8 * ti[u] <= c) {
+#pragma unroll
+                for (int ii = 0; ii < 8; ++ii)
+                    if (8 * ti[u] + ii <= c) li[ii] = Real(0);
+            }
+#pragma unroll
+            for (int ii = 0; ii < 8; ++ii) {
+                const Real l = li[ii] * ip;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) acc[u][ii][kk] -= l * lk[kk];
+            }
+        }
+    }
+    if (t >= 32) return;
+    if (fail) {
+        if (lane == 0) {
+            a.status = FBSDE_ERR_CG;
+            a.done = 1;
+        }
+        return;   // x stays 0 from the setup
+    }
+    // L y = rhs, z = D^{-1} y, L^T x = z with L_ic = Lc[c][i] / D_c; lane l holds the
+    // entries l, l + 32, l + 64, l + 96 of y (then z, then x) in registers
+    constexpr int kV = kDirMaxD / 32;
+    Real yv[kV], invD[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        const int i = lane + 32 * v;
+        yv[v] = i < d ? rhs[o + i] : Real(0);
+        invD[v] = i < d ? Real(1) / Lc[i * dp + i] : Real(0);
+    }
+    for (int c = 0; c < d; ++c) {
+        Real yc = Real(0);
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            if ((c >> 5) == v) yc = __shfl_sync(0xffffffffu, yv[v] * invD[v], c & 31);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int i = lane + 32 * v;
+            if (i > c && i < d) yv[v] -= Lc[c * dp + i] * yc;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) yv[v] *= invD[v];
+    for (int c = d - 1; c > 0; --c) {   // x_c is final once the entries below are in
+        Real xc = Real(0);
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            if ((c >> 5) == v) xc = __shfl_sync(0xffffffffu, yv[v], c & 31);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int k = lane + 32 * v;
+            if (k < c) yv[v] -= Lc[k * dp + c] * invD[v] * xc;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        const int i = lane + 32 * v;
+        if (i < d) x[o + i] = yv[v];
+    }
+}
+
 // Per anchor: alpha = c - S . x (Eq. 3.20), Z = sigma x, the features of f at
 // (t_k, X_k^m, Z) and Newton (2.16)-(2.17) for Y_k^m (lane 0).
 template <typename Real>
@@ -888,7 +1130,7 @@ CgShape cg_shape(int nchk)
 template <typename Real>
 cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
                      uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
-                     cudaStream_t b, long long Kb)
+                     cudaStream_t b, long long Kb, bool direct)
 {
     cudaError_t e;
     Params p = params_of(Pb, L, seed);
@@ -917,7 +1159,16 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
     // batch reading: the products cover only the band of entries the windows use (tiles and
     // K-splits off it are skipped); T's entries off the band stay zero for the whole solve
     const dev::Band band{(long long)M, Kb < M ? Kb : (long long)M};
-    if (fused && Kb < M) ANC_TRY(cudaMemsetAsync(T, 0, (size_t)M * M * sizeof(Real), s));
+    if (fused && Kb < M && !direct)
+        ANC_TRY(cudaMemsetAsync(T, 0, (size_t)M * M * sizeof(Real), s));
+    // direct batch solve: one 8 x 4 tile per thread while the triangle has at most
+    // kDirThreads of them (fewer registers and threads, more blocks per SM), else two
+    const size_t dir_smem = dir_smem_bytes(L.d, sizeof(Real));
+    const int dir_nI = dir_pad(L.d) / 8;
+    const bool dir_two = dir_nI * (dir_nI + 1) > kDirThreads;
+    if (direct)
+        ANC_TRY(cudaFuncSetAttribute(dir_two ? k_anc_direct<Real, 2> : k_anc_direct<Real, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dir_smem));
     const CgShape cg = cg_shape(ld / Chunk<Real>::E);
     for (int k = L.N - 1; k >= 0; --k) {
         const double t_k = k * p.dt;
@@ -936,8 +1187,16 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
                                                            rhs, x, r, pv);
         ANC_TRY(cudaGetLastError());
         // the CG passes: a conditional while node (body on b) that repeats while some anchor
-        // iterates on and fewer than cg_max_iter passes ran
-        {
+        // iterates on and fewer than cg_max_iter passes ran; or each anchor's direct solve
+        if (direct) {
+            if (dir_two)
+                k_anc_direct<Real, 2><<<M, kDirThreads, dir_smem, s>>>(p, band.Kb, P, A, W, S, rhs,
+                                                                       st, x);
+            else
+                k_anc_direct<Real, 1><<<M, 32 * ((dir_nI * (dir_nI + 1) + 31) / 32), dir_smem, s>>>(
+                    p, band.Kb, P, A, W, S, rhs, st, x);
+            ANC_TRY(cudaGetLastError());
+        } else {
             cudaStreamCaptureStatus cst;
             cudaGraph_t g = nullptr;
             const cudaGraphNode_t *deps = nullptr;
@@ -1019,7 +1278,7 @@ cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, ui
 // Every query of a call, enqueued on the capturing stream s (bodies on b): the counters and
 // the status word are cleared once, then the queries run one after the other on the
 // shared workspace.
-cudaError_t emit_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t Q,
+cudaError_t emit_call(const fbsde_problem *P, const Lay &L, int64_t K, bool direct, int32_t Q,
                       const double *x0, uint64_t seed, uint32_t solve_index0, double *u0,
                       double *grad_u0, char *ws, cudaStream_t s, cudaStream_t b)
 {
@@ -1029,8 +1288,9 @@ cudaError_t emit_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t Q
         const double *xq = x0 + (size_t)q * P->d;
         double *gq = grad_u0 ? grad_u0 + (size_t)q * P->d : nullptr;
         e = P->precision == FBSDE_FP32
-                ? emit_one<float>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K)
-                : emit_one<double>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K);
+                ? emit_one<float>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K, direct)
+                : emit_one<double>(P, L, xq, seed, solve_index0 + q, u0 + q, gq, ws, s, b, K,
+                                   direct);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1060,7 +1320,7 @@ template <typename T> void put(std::vector<unsigned char> &k, const T &v)
     k.insert(k.end(), b, b + sizeof(T));
 }
 
-cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t Q,
+cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, bool direct, int32_t Q,
                         const double *x0, uint64_t seed, uint32_t solve_index0, double *u0,
                         double *grad_u0, char *ws, cudaStream_t s)
 {
@@ -1078,10 +1338,12 @@ cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return e;
     if (cs == cudaStreamCaptureStatusActive)   // the caller is capturing: become part of it
-        return emit_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0, ws, s, g_anc->body[dev]);
+        return emit_call(P, L, K, direct, Q, x0, seed, solve_index0, u0, grad_u0, ws, s,
+                         g_anc->body[dev]);
     std::vector<unsigned char> key;
     put(key, *P);
     put(key, K);
+    put(key, direct);
     put(key, Q);
     put(key, x0);
     put(key, seed);
@@ -1096,7 +1358,8 @@ cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t
         cudaStream_t c = g_anc->cap[dev];
         if ((e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
         const cudaError_t ec =
-            emit_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0, ws, c, g_anc->body[dev]);
+            emit_call(P, L, K, direct, Q, x0, seed, solve_index0, u0, grad_u0, ws, c,
+                      g_anc->body[dev]);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(c, &g);
         if (ec != cudaSuccess || e != cudaSuccess || !g) {
@@ -1128,6 +1391,26 @@ cudaError_t launch_call(const fbsde_problem *P, const Lay &L, int64_t K, int32_t
     return cudaEventRecord(it->last, s);
 }
 
+// fbsde_solve_batch and fbsde_solve_batch_direct: argument checks, then the call's graph.
+int solve_batch(const fbsde_problem *P, int64_t K, bool direct, int32_t Q, const double *x0,
+                uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
+                void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
+{
+    Lay L;
+    if (!lay(P, L) || Q < 1 || !x0 || !u0) return FBSDE_ERR_ARG;
+    if (K < 2 || K > L.M) return FBSDE_ERR_ARG;
+    // the direct factorisation needs a positive ridge: it bounds every pivot below by lambda_m
+    if (direct && (P->d > kDirMaxD || !(P->ridge_rel > 0.0))) return FBSDE_ERR_ARG;
+    if ((P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) && !P->theta)
+        return FBSDE_ERR_ARG;
+    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAl))
+        return FBSDE_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const cudaError_t e = launch_call(P, L, K, direct, Q, x0, seed, solve_index0, u0, grad_u0,
+                                      static_cast<char *>(workspace), s);
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace anchored
 }  // namespace fbsde
@@ -1151,21 +1434,22 @@ int fbsde_solve_anchored(const fbsde_problem *P, int32_t Q, const double *x0, ui
              : FBSDE_ERR_ARG;
 }
 
+
 int fbsde_solve_batch(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
                       uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
                       void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
 {
-    Lay L;
-    if (!lay(P, L) || Q < 1 || !x0 || !u0) return FBSDE_ERR_ARG;
-    if (K < 2 || K > L.M) return FBSDE_ERR_ARG;
-    if ((P->kind == FBSDE_HJB_LOGQUAD || P->kind == FBSDE_AFFINE_TEST) && !P->theta)
-        return FBSDE_ERR_ARG;
-    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAl))
-        return FBSDE_ERR_WORKSPACE;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const cudaError_t e = launch_call(P, L, K, Q, x0, seed, solve_index0, u0, grad_u0,
-                                      static_cast<char *>(workspace), s);
-    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+    return solve_batch(P, K, false, Q, x0, seed, solve_index0, u0, grad_u0, workspace,
+                       workspace_bytes, stream);
+}
+
+int fbsde_solve_batch_direct(const fbsde_problem *P, int64_t K, int32_t Q, const double *x0,
+                             uint64_t seed, uint32_t solve_index0, double *u0, double *grad_u0,
+                             void *workspace, size_t workspace_bytes, fbsde_stream_t stream)
+{
+    static_assert(kDirMaxD == FBSDE_BATCH_DIRECT_MAX_D, "the header's limit");
+    return solve_batch(P, K, true, Q, x0, seed, solve_index0, u0, grad_u0, workspace,
+                       workspace_bytes, stream);
 }
 
 int fbsde_anchored_diagnostics(const fbsde_problem *P, const void *workspace, fbsde_diag *out,

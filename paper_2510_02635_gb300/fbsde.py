@@ -76,11 +76,11 @@ EXPORTS = ["fbsde_workspace_bytes", "fbsde_solve", "fbsde_solve_host",
            "fbsde_plan_workspace_bytes", "fbsde_plan_create", "fbsde_plan_launch",
            "fbsde_plan_diagnostics", "fbsde_plan_destroy", "fbsde_plan_instance_diagnostics",
            "fbsde_anchored_workspace_bytes", "fbsde_solve_anchored", "fbsde_solve_batch",
-           "fbsde_anchored_diagnostics", "fbsde_check_bounded_wait"]
+           "fbsde_solve_batch_direct", "fbsde_anchored_diagnostics", "fbsde_check_bounded_wait"]
 FBSDE_NOALLOC_MAX_BYTES = 64 << 20
 FBSDE_NUM_KERNELS = 13
-FBSDE_MAX_D = 16384
 FBSDE_MAX_D_FP64 = 10240
+FBSDE_BATCH_DIRECT_MAX_D = 128
 FBSDE_PROFILED_EAGER_PASSES = 48   # the header constant of the same name
 
 _lock = threading.Lock()
@@ -131,6 +131,8 @@ def load_library(path: str = LIB_PATH):
         lib.fbsde_solve_anchored.restype = C.c_int
         lib.fbsde_solve_batch.argtypes = [P, C.c_int64, I32, V, U64, U32, V, V, V, SZ, V]
         lib.fbsde_solve_batch.restype = C.c_int
+        lib.fbsde_solve_batch_direct.argtypes = [P, C.c_int64, I32, V, U64, U32, V, V, V, SZ, V]
+        lib.fbsde_solve_batch_direct.restype = C.c_int
         lib.fbsde_anchored_diagnostics.argtypes = [P, V, C.POINTER(fbsde_diag), V]
         lib.fbsde_anchored_diagnostics.restype = C.c_int
         lib.fbsde_check_bounded_wait.argtypes = [I64, V, C.POINTER(C.c_int64), V]
@@ -253,6 +255,16 @@ def fbsde_solve_batch(problem: fbsde_problem, K: int, Q: int, x0, seed: int, sol
         _stream(stream)))
 
 
+def fbsde_solve_batch_direct(problem: fbsde_problem, K: int, Q: int, x0, seed: int,
+                             solve_index0: int, u0, grad_u0, workspace, stream=None) -> int:
+    """The batch reading with each anchor's regression solved directly (L D L^T of its
+    operator; d <= FBSDE_BATCH_DIRECT_MAX_D; asynchronous)."""
+    return int(load_library().fbsde_solve_batch_direct(
+        C.byref(problem), int(K), int(Q), _ptr(x0), int(seed), int(solve_index0), _ptr(u0),
+        _ptr(grad_u0), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream)))
+
+
 def fbsde_anchored_diagnostics(problem: fbsde_problem, workspace, stream=None) -> fbsde_diag:
     out = fbsde_diag()
     check(load_library().fbsde_anchored_diagnostics(C.byref(problem), _ptr(workspace),
@@ -262,9 +274,10 @@ def fbsde_anchored_diagnostics(problem: fbsde_problem, workspace, stream=None) -
 
 
 def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0,
-                   K: int | None = None) -> dict:
+                   K: int | None = None, direct: bool = False) -> dict:
     """Per-anchor solve of the CUDA tensor x0 [Q, d]; returns u0 [Q], grad [Q, d], status.
-    With K, each anchor's regression runs over its batch of K particles (fbsde_solve_batch)."""
+    With K, each anchor's regression runs over its batch of K particles (fbsde_solve_batch),
+    or, with direct, is solved directly (fbsde_solve_batch_direct)."""
     import torch
     Q = x0.shape[0]
     nbytes = fbsde_anchored_workspace_bytes(problem)
@@ -276,6 +289,9 @@ def solve_anchored(problem: fbsde_problem, x0, seed: int, solve_index0: int = 0,
     if K is None:
         check(fbsde_solve_anchored(problem, Q, x0, seed, solve_index0, u, g, ws),
               "fbsde_solve_anchored")
+    elif direct:
+        check(fbsde_solve_batch_direct(problem, K, Q, x0, seed, solve_index0, u, g, ws),
+              "fbsde_solve_batch_direct")
     else:
         check(fbsde_solve_batch(problem, K, Q, x0, seed, solve_index0, u, g, ws),
               "fbsde_solve_batch")
@@ -581,6 +597,12 @@ def _main(argv=None) -> None:
     ap.add_argument("--anchored", action="store_true",
                     help="Algorithm 1 with one regression per particle anchor "
                          "(fbsde_solve_anchored)")
+    ap.add_argument("--K", type=int, default=0,
+                    help="with --anchored: each anchor's regression over its batch of K "
+                         "particles (fbsde_solve_batch)")
+    ap.add_argument("--direct", action="store_true",
+                    help="with --anchored --K: solve each batch regression directly "
+                         "(fbsde_solve_batch_direct)")
     ap.add_argument("--time-products", action="store_true",
                     help="run the launch profiler on the product kernel (the first "
                          "FBSDE_PROFILED_EAGER_PASSES CG passes of each level are then launched "
@@ -615,15 +637,16 @@ def _main(argv=None) -> None:
             fbsde_profile_select([a.time_family or "matvec"])
     for r in range(a.repeat):
         t0 = time.perf_counter()
-        out = (solve_anchored(solver.problem, x0, a.seed) if a.anchored
-               else solver.solve(x0, seed=a.seed))
+        out = (solve_anchored(solver.problem, x0, a.seed, K=a.K or None, direct=a.direct)
+               if a.anchored else solver.solve(x0, seed=a.seed))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         print(f"solve {r}: {dt * 1e3:.1f} ms status={out['status']} "
               f"u0[0]={float(out['u0'][0]):.12f}")
     if a.kernel_table:
         from torch.profiler import ProfilerActivity, profile
-        run = ((lambda: solve_anchored(solver.problem, x0, a.seed)) if a.anchored
+        run = ((lambda: solve_anchored(solver.problem, x0, a.seed, K=a.K or None,
+                                       direct=a.direct)) if a.anchored
                else (lambda: solver.solve(x0, seed=a.seed)))
         with profile(activities=[ProfilerActivity.CUDA]) as kp:
             run()

@@ -47,7 +47,7 @@ def test_binding_constants_match_the_header():
 
 
 def test_abi_version_and_status_strings(lib):
-    assert fbsde.fbsde_abi_version() == 2
+    assert fbsde.fbsde_abi_version() == 3
     assert fbsde.fbsde_status_string(0) == "ok"
     assert "argument" in fbsde.fbsde_status_string(1)
     assert fbsde.fbsde_status_string(99) == "unknown status"

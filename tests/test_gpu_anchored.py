@@ -1,8 +1,9 @@
 """Algorithm 1 with one regression per particle anchor: the CUDA path against the oracle's
 literal per-anchor solve on the same seeds (FP64 within 1e-10, FP32 within 1e-4), and, with
 uniform weights, against the single-anchor entry point; the same for each anchor's
-regression over a batch of K particles (fbsde_solve_batch against the oracle's subset loop).  Sizes are ragged with respect to
-the 64 x 64 tiles of the SIMT contractions, the 128 x 128 tiles of the tensor-core ones
+regression over a batch of K particles (fbsde_solve_batch, and fbsde_solve_batch_direct with
+each regression solved directly, against the oracle's subset loop).  Sizes are ragged with
+respect to the 64 x 64 tiles of the SIMT contractions, the 128 x 128 tiles of the tensor-core ones
 (M >= 1024, FP32) and the 16-byte row chunks."""
 import math
 
@@ -25,7 +26,7 @@ CASES = [
 ]
 
 
-def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13, K=None):
+def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13, K=None, direct=False):
     extra = dict(extra)
     sigma, T, h = extra.pop("sigma", 1.0), extra.pop("T", 0.5), extra.pop("h", 2.0)
     rng = np.random.default_rng(d * 1000 + M)
@@ -35,7 +36,7 @@ def _run(fb, kind, d, M, N, prec, extra, Q=2, seed=13, K=None):
     th_dev = torch.tensor(theta, device="cuda") if theta is not None else None
     p = fb.make_problem(kind, d, N, M, sigma, T, prec, theta=th_dev, h=h, cg_tol=tol,
                         cg_max_iter=1000, **extra)
-    out = fb.solve_anchored(p, torch.tensor(x0, device="cuda"), seed, 0, K=K)
+    out = fb.solve_anchored(p, torch.tensor(x0, device="cuda"), seed, 0, K=K, direct=direct)
     torch.cuda.synchronize()
     op = oracle.Problem(kind, d, sigma, T, N, M, theta=theta, h=h, cg_tol=1e-13,
                         cg_max_iter=1000, **extra)
@@ -184,6 +185,60 @@ def test_banded_products_match_oracle(prec, tol, M, K):
     from paper_2510_02635_gb300 import fbsde as fb
     out, refs, *_ = _run(fb, "ac_manufactured", 24, M, 2, prec, {}, Q=1, K=K)
     _check(out, refs, tol)
+
+
+@pytest.mark.parametrize("kind,d,M,N,K,extra", BATCH_CASES)
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32", TOL_FP32)])
+def test_direct_batch_matches_oracle(kind, d, M, N, K, extra, prec, tol):
+    """Each anchor's batch regression solved directly (its operator's L D L^T) against the
+    oracle's literal subset loop, on the cases of the CG form."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, kind, d, M, N, prec, extra, K=K, direct=True)
+    _check(out, refs, tol)
+    assert out["cg_passes"] == 0
+
+
+@pytest.mark.parametrize("prec,tol,d,M,K", [
+    ("fp64", TOL_FP64, 16, 65, 2),       # K = 2 < d: held by the ridge
+    ("fp32", TOL_FP32, 21, 1030, 300),   # tensor-core products of the level
+    ("fp32", TOL_FP32, 24, 1300, 40),    # banded products, the band wrapping around
+    ("fp64", TOL_FP64, 128, 160, 48),    # the largest d: three 4 x 4 blocks per thread
+    ("fp32", TOL_FP32, 127, 200, 150),   # ragged d, padding inside the last block
+])
+def test_direct_batch_edges_match_oracle(prec, tol, d, M, K):
+    from paper_2510_02635_gb300 import fbsde as fb
+    out, refs, *_ = _run(fb, "ac_manufactured", d, M, 2, prec, {}, Q=1, K=K, direct=True)
+    _check(out, refs, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32", TOL_FP32)])
+def test_direct_and_cg_batch_solve_the_same_regressions(prec, tol):
+    """The two forms of the batch reading agree (the CG to its tolerance, the direct solve
+    to rounding), on a window wider than d."""
+    from paper_2510_02635_gb300 import fbsde as fb
+    d, M, N, Q, K = 50, 600, 3, 2, 200
+    x0 = torch.tensor(np.random.default_rng(8).normal(scale=0.3, size=(Q, d)), device="cuda")
+    p = fb.make_problem("ac_manufactured", d, N, M, 1.0, 0.5, prec,
+                        cg_tol=1e-13 if prec == "fp64" else 1e-7, cg_max_iter=1000)
+    a = fb.solve_anchored(p, x0, 4, 0, K=K)
+    b = fb.solve_anchored(p, x0, 4, 0, K=K, direct=True)
+    assert a["status"] == 0 and b["status"] == 0
+    assert torch.all(torch.abs(a["u0"] - b["u0"]) <= tol * torch.abs(a["u0"]))
+    scale = torch.maximum(torch.linalg.norm(a["grad"], dim=1), torch.abs(a["u0"]))
+    assert torch.all(torch.linalg.norm(a["grad"] - b["grad"], dim=1) <= tol * scale)
+
+
+def test_direct_batch_argument_errors():
+    from paper_2510_02635_gb300 import fbsde as fb
+    Q = 1
+    for d, ridge in ((fb.FBSDE_BATCH_DIRECT_MAX_D + 1, 1e-3), (16, 0.0)):
+        p = fb.make_problem("ac_manufactured", d, 2, 100, 1.0, 0.5, "fp32", ridge_rel=ridge)
+        ws = torch.empty(fb.fbsde_anchored_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+        x0 = torch.zeros(Q, d, dtype=torch.float64, device="cuda")
+        u = torch.empty(Q, dtype=torch.float64, device="cuda")
+        g = torch.empty(Q, d, dtype=torch.float64, device="cuda")
+        assert fb.fbsde_solve_batch_direct(p, 50, Q, x0, 1, 0, u, g, ws) == fb.FBSDE_ERR_ARG
+        assert fb.fbsde_solve_batch_direct(p, 1, Q, x0, 1, 0, u, g, ws) == fb.FBSDE_ERR_ARG
 
 
 @pytest.mark.parametrize("prec,M", [("fp64", 300), ("fp32", 1100)])
