@@ -54,13 +54,12 @@ struct SolveState {
     double c, alpha, lambda, invW, rr, rhs2, sp, yref, sumz, zz, phi0, gx0;
     double abar, sv, sumz_l, zz_l;  // reverse sweep
     double rr_prev, cg_alpha;       // previous r . r and step of the CG recurrence
-    double cg_beta, cg_step;        // scalars of the current CG pass
     double sx;                      // S . x of the adjoint solve's starting guess
     double rho_ref;                 // forward SDE: mean squared distance to the anchor
     double sum_ax, ax_x0;           // forward SDE: sum_i alpha_x,i and alpha_x . x0
     double psi0;                    // forward SDE: second feature of f at x0 (kinds 7, 8)
     int32_t iters, done, status, newton_max, cg_exhausted, newton_max_all, loop_iter, cg_total, arrive,
-        arrive_q, cg_ok, pad4;
+        arrive_q;
 };
 
 struct Layout {

@@ -925,11 +925,8 @@ __global__ void __launch_bounds__(256) k_moments(Params p)
 //   cg_mode = 0: vectors 0..nvec-1 into v64 slots dst0..
 //   cg_mode = 1: the product of the CG pass (queries already converged skip):
 //       w = sum / W - S (S . r) + lambda r   (Gamma_c r + lambda r, Eq. 3.19's operator)
-//     into slot 5 and this block's share of w . r into bpart; the last block of the query
-//     to finish adds the shares (delta = w . r) and derives the scalars of the pass of
-//     k_cg_update (Chronopoulos and Gear 1989): with gamma = r . r,
-//       t = 0: beta = 0, a = gamma / delta;
-//       t > 0: beta = gamma / gamma_prev, a = gamma / (delta - beta gamma / a_prev).
+//     into slot 5 and this block's share of w . r into bpart; every block of k_cg_update
+//     adds the shares and derives the pass's scalars from them.
 // Grid (nblk, Q), nblk = ceil(ld / kRedTile).
 template <typename Real> struct RedAcc {
     double s;
@@ -986,7 +983,6 @@ __global__ void __launch_bounds__(512) k_reduce_partials(Params p, int nvec, int
     __shared__ Real sh_s[16][kRedTile];
     __shared__ Lo sh_c[16][kRedTile];
     __shared__ double sh_w[4];
-    __shared__ int last_sh;
     const int s = blockIdx.y;
     SolveState &st = p.st[s];
     if (cg_mode && st.done) return;
@@ -1045,32 +1041,8 @@ __global__ void __launch_bounds__(512) k_reduce_partials(Params p, int nvec, int
         __syncthreads();
     }
     if (!cg_mode) return;
-    double *bp = p.bpart + (size_t)s * p.nblk * kBpart;
-    if (threadIdx.x == 0) {
-        bp[(size_t)blockIdx.x * kBpart] = ((sh_w[0] + sh_w[1]) + sh_w[2]) + sh_w[3];
-        __threadfence();
-        last_sh = atomicAdd(&st.arrive_q, 1) == p.nblk - 1;
-    }
-    __syncthreads();
-    if (!last_sh || threadIdx.x >= 32) return;
-    __threadfence();
-    double dl = 0.0;
-    for (int b = lane; b < p.nblk; b += 32) dl += __ldcg(bp + (size_t)b * kBpart);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
-    if (lane == 0) {
-        const double gam = st.rr;
-        double beta = 0.0, den = dl;
-        if (st.iters > 0) {
-            beta = gam / st.rr_prev;
-            den = dl - beta * gam / st.cg_alpha;
-        }
-        const double a = gam / den;
-        st.cg_beta = beta;
-        st.cg_step = a;
-        st.cg_ok = (den > 0.0 && isfinite(a)) ? 1 : 0;
-        st.arrive_q = 0;
-    }
+    if (threadIdx.x == 0)   // the next kernel boundary makes the shares visible
+        p.bpart[((size_t)s * p.nblk + blockIdx.x) * kBpart] = ((sh_w[0] + sh_w[1]) + sh_w[2]) + sh_w[3];
 }
 
 // ---------------------------------------------------------------------------
@@ -1236,7 +1208,11 @@ __device__ __forceinline__ void st4(float *q, const float (&v)[4])
 
 // One pass of the CG iteration of Chronopoulos and Gear (1989), the form of conjugate
 // gradients with a single reduction phase per iteration.  The product w = A r and the
-// scalars beta, a of the pass come from k_reduce_partials; here
+// shares of delta = w . r come from k_reduce_partials; every block adds the shares in
+// the same order and derives the pass's scalars (gamma = r . r):
+//   t = 0: beta = 0, a = gamma / delta;
+//   t > 0: beta = gamma / gamma_prev, a = gamma / (delta - beta gamma / a_prev),
+// then
 //   p = r + beta p,  s = w + beta s (= A p),  x += a p,  r -= a s,
 // one warp per tile of kRedTile elements (four consecutive elements per lane), with the
 // tile's shares of S . r and r . r for the next pass.  The last block of the query to
@@ -1245,7 +1221,8 @@ __device__ __forceinline__ void st4(float *q, const float (&v)[4])
 // FP64 warp instruction occupies the SM's FP64 pipe for many cycles on this part, so the
 // scalar work is done once per query (in the reduction) rather than once per block.  In a
 // CUDA graph (use_h = 1) the last query to finish sets the while-loop condition: 1 while
-// some query has not converged and fewer than cg_max_iter passes ran.  Grid (nblk, Q).
+// some query has not converged and fewer than cg_max_iter passes ran (with one query,
+// its last block does so without the second arrival).  Grid (nblk, Q).
 template <typename Real>
 __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditionalHandle h, int use_h)
 {
@@ -1260,15 +1237,15 @@ __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditional
                *w = ws.v64(s, 5), *sv = ws.v64(s, 7);
         Real *rR = ws.vR(s, 0);
         double *bp = p.bpart + (size_t)s * p.nblk * kBpart;
-        const int t = st.iters, ok = st.cg_ok;
-        const double beta = st.cg_beta, a = st.cg_step, gam = st.rr;
+        const int t = st.iters;
+        const double gam = st.rr;
         const int i0 = blockIdx.x * kRedTile + 4 * lane;
-        double sr = 0.0, rr = 0.0;
-        if (ok && i0 < p.ld) {  // ld is a multiple of 4
-            // every value of the lane's four elements is loaded before the first store
-            // (the vectors may alias as far as the compiler can tell, so it would not
-            // move a later element's loads above an earlier element's stores)
-            double rv[4], wv[4], pv[4], svv[4], xv[4], Sv[4];
+        const bool in = i0 < p.ld;   // ld is a multiple of 4
+        // every value of the lane's four elements is loaded first, before the pass's scalars
+        // are derived and before the first store (the vectors may alias as far as the
+        // compiler can tell, so it would not move a later element's loads above a store)
+        double rv[4], wv[4], pv[4], svv[4], xv[4], Sv[4];
+        if (in) {
             ld4(rv, r + i0);
             ld4(wv, w + i0);
             ld4(xv, x + i0);
@@ -1277,6 +1254,20 @@ __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditional
                 ld4(pv, pp + i0);
                 ld4(svv, sv + i0);
             }
+        }
+        double dl = 0.0;   // delta = w . r: the shares in a fixed order, the same in every block
+        for (int b = lane; b < p.nblk; b += 32) dl += __ldcg(bp + (size_t)b * kBpart);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+        double beta = 0.0, den = dl;
+        if (t > 0) {
+            beta = gam / st.rr_prev;
+            den = dl - beta * gam / st.cg_alpha;
+        }
+        const double a = gam / den;
+        const int ok = (den > 0.0 && isfinite(a)) ? 1 : 0;
+        double sr = 0.0, rr = 0.0;
+        if (ok && in) {
             Real rn4[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -1347,10 +1338,13 @@ __global__ void __launch_bounds__(32) k_cg_update(Params p, cudaGraphConditional
         }
     }
     if (use_h && global_arrive && lane == 0) {
-        __threadfence();
-        const int arrived = atomicAdd(&p.st[0].arrive, 1);
-        if (arrived == p.Q - 1) {
+        bool last_q = true;   // one query: its last block is the last arrival
+        if (p.Q > 1) {
             __threadfence();
+            last_q = atomicAdd(&p.st[0].arrive, 1) == p.Q - 1;
+        }
+        if (last_q) {
+            if (p.Q > 1) __threadfence();
             p.st[0].arrive = 0;
             const int count = ++p.st[0].loop_iter;
             bool active = false;
