@@ -228,9 +228,11 @@ __global__ void __launch_bounds__(128) k_anc_rows(Params p, const Real *P, const
 //   mode 1: T_jm = w_jm (G_jm - A_m . v_m) / W_m stored in T; sum T.
 constexpr int kRowChunk = 64;
 template <typename Real>
-__global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, const Real *G,
-                              const double *pn, const double *an, const double *Y, Real *W,
-                              Real *T, const Anchor *st, double *part)
+__global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb,
+                              const Real *__restrict__ G, const double *__restrict__ pn,
+                              const double *__restrict__ an, const double *__restrict__ Y,
+                              Real *__restrict__ W, Real *__restrict__ T, const Anchor *st,
+                              double *part)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
@@ -243,6 +245,7 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, 
         Real sw = 0, swy = 0, swr = 0;
         const Real am = (Real)an[m], ref = (Real)rho_ref;
         const Real scale = p.uniform ? Real(0) : (Real)(-1.0 / (p.h2 * rho_ref));
+#pragma unroll 8
         for (long long j = j0; j < j1; ++j) {
             long long off = j - m;   // position of particle j in anchor m's window
             if (off < 0) off += p.M;
@@ -264,6 +267,7 @@ __global__ void k_anc_columns(Params p, int mode, double rho_ref, long long Kb, 
         if (a.done) return;
         const Real inv = (Real)(1.0 / a.W), ap = (Real)a.ap;
         Real sum = 0;
+#pragma unroll 8
         for (long long j = j0; j < j1; ++j) {
             const size_t ix = (size_t)j * p.M + m;
             long long off = j - m;
@@ -850,11 +854,13 @@ __global__ void __launch_bounds__(32 * kAncWarps) k_anc_newton(Params p, double 
     if (m >= p.M) return;
     Anchor &a = st[m];
     const size_t o = (size_t)m * p.ld;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // S . x, sum cos(x0 + A), sum x, |x|^2
+    // S . x, sum cos(x0 + A), sum x, |x|^2: lane sums and the warp tree in the stream
+    // precision (as the per-anchor vectors themselves), widened once
+    Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
     for (int i = lane; i < p.ld; i += 32) {
-        const double xi = (double)x[o + i];
-        acc[0] += (double)S[o + i] * xi;
-        if (i < p.d) acc[1] += (double)dev::cos_stream((Real)x0[i] + A[o + i]);
+        const Real xi = x[o + i];
+        acc[0] += S[o + i] * xi;
+        if (i < p.d) acc[1] += dev::cos_stream((Real)x0[i] + A[o + i]);
         acc[2] += xi;
         acc[3] += xi * xi;
     }
