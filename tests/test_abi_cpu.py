@@ -197,6 +197,25 @@ def test_batch_argument_errors_return_synchronously(lib):
     assert lib.fbsde_solve_batch(None, 64, 1, fake, 0, 0, fake, None, fake, n, None) == 1
 
 
+def test_direct_batch_argument_errors_return_synchronously(lib):
+    """The direct form takes the batch form's checks, and also needs d <= 128 and a positive
+    ridge (the ridge bounds every pivot of its factorisation below)."""
+    fake = C.c_void_p(1 << 20)
+    p = _prob(M=256)
+    n = fbsde.fbsde_anchored_workspace_bytes(p)
+    for K in (1, 0, 257):
+        assert lib.fbsde_solve_batch_direct(C.byref(p), K, 1, fake, 0, 0, fake, None, fake, n,
+                                            None) == 1
+    assert lib.fbsde_solve_batch_direct(C.byref(p), 64, 1, fake, 0, 0, fake, None, fake, n - 1,
+                                        None) == 2
+    for bad in (dict(d=fbsde.FBSDE_BATCH_DIRECT_MAX_D + 1), dict(ridge_rel=0.0)):
+        pb = _prob(M=256, **bad)
+        nb = fbsde.fbsde_anchored_workspace_bytes(pb)
+        assert nb > 0   # the CG form takes these problems
+        assert lib.fbsde_solve_batch_direct(C.byref(pb), 64, 1, fake, 0, 0, fake, None, fake, nb,
+                                            None) == 1
+
+
 def test_forward_sde_workspace_and_argument_checks(lib):
     """A drift, a state-dependent diffusion or a drift kind adds the stored levels of the
     Euler-Maruyama rows (checkpoints every s = ceil(sqrt N) levels below N plus one segment
