@@ -1115,10 +1115,6 @@ __global__ void k_anc_loop_next(int *cnt, int max_iter, cudaGraphConditionalHand
     cudaGraphSetConditional(h, (active > 0 && passes < max_iter) ? 1u : 0u);
 }
 
-// One query, enqueued on s, which must be capturing into a CUDA graph: the forward sweep,
-// then the levels k = N-1..0, each level's CG passes as a conditional while node whose
-// body is captured on the stream b.  The device status accumulates in cnt[1].
-// Kb: particles per anchor's regression (the cyclic window; Kb = M: all of them).
 // Block of the register-resident CG pass for rows of nchk 16-byte chunks: nw warps and C
 // chunks per thread with 32 nw C >= nchk, C in {1, 2, 4} and nw <= 8 (C = 0: rows longer
 // than 1024 chunks, which take the streaming k_anc_cg).
@@ -1133,6 +1129,10 @@ CgShape cg_shape(int nchk)
     return {nw, per <= 1 ? 1 : per <= 2 ? 2 : 4};
 }
 
+// One query, enqueued on s, which must be capturing into a CUDA graph: the forward sweep,
+// then the levels k = N-1..0, each level's CG passes as a conditional while node whose
+// body is captured on the stream b.  The device status accumulates in cnt[1].
+// Kb: particles per anchor's regression (the cyclic window; Kb = M: all of them).
 template <typename Real>
 cudaError_t emit_one(const fbsde_problem *Pb, const Lay &L, const double *x0, uint64_t seed,
                      uint32_t sidx, double *u0, double *grad, char *ws, cudaStream_t s,
