@@ -802,7 +802,7 @@ template <typename Real, int VM>
 __global__ void __launch_bounds__(256) k_moments(Params p)
 {
     constexpr int E = Chunk<Real>::E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tile = blockIdx.x, g = blockIdx.y, s = blockIdx.z;
     const WS<Real> ws(p);
     const int nch = p.ld / E;
