@@ -618,6 +618,10 @@ def _main(argv=None) -> None:
                          "profiler (torch.profiler): device time per kernel, including the "
                          "kernels that CUDA graphs launch")
     a = ap.parse_args(argv)
+    if a.K and not a.anchored:
+        ap.error("--K needs --anchored")
+    if a.direct and not a.K:
+        ap.error("--direct needs --K")
     rng = np.random.default_rng(a.seed)
     x0 = torch.tensor(rng.uniform(-1.0, 1.0, size=(a.Q, a.d)) if a.x0 == "uniform"
                       else np.zeros((a.Q, a.d)), device="cuda")

@@ -258,3 +258,12 @@ def test_bounded_wait_check_argument_errors(lib):
     assert lib.fbsde_check_bounded_wait(2_000_000_000, fake, None, None) == 1
     assert lib.fbsde_check_bounded_wait(1000, None, None, None) == 1
     assert lib.fbsde_check_bounded_wait(1000, C.c_void_p((1 << 20) + 4), None, None) == 1
+
+
+@pytest.mark.parametrize("argv", [["--K", "64"], ["--anchored", "--direct"], ["--direct"]])
+def test_cli_rejects_batch_options_without_their_form(argv):
+    """The CLI's batch options apply to the per-anchor form only: --K needs --anchored and
+    --direct needs --K (an argument error before any device work)."""
+    with pytest.raises(SystemExit) as e:
+        fbsde._main(argv)
+    assert e.value.code == 2
